@@ -1,0 +1,79 @@
+"""End-to-end pins: the oracle's EXCMG reproduces the errors printed in Tables 1-10."""
+import collections
+
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import read_golden
+from paper_1507_05063_gb300 import problems as P
+
+# tolerance of each table (Section 5 text / table captions) and coarsest grid
+SETUP = {"ex1": (1e-14, (4, 4, 4)), "ex2": (1e-14, (4, 4, 4)), "ex3": (1e-11, (4, 4, 4)),
+         "ex4": (1e-9, (8, 4, 2)), "ex5": (1e-12, (4, 4, 4)), "ex6": (1e-13, (4, 4, 4))}
+
+
+def _rows():
+    groups = collections.defaultdict(list)
+    for ex, mesh, norm, qty, val, src in read_golden("paper_tables.txt"):
+        groups[(ex, mesh)].append((norm, qty, float(val), src))
+    return sorted(groups.items())
+
+
+def errors_of_run(name, N):
+    eps, N0 = SETUP[name]
+    prob = P.PROBLEMS[name]
+    f, g, u = P.make_inputs(prob, N)
+    res = O.excmg(f, g, (1.0, 1.0, 1.0), N, N0, eps=eps, eps_coarse=eps)
+    uh, ut, w = res["u"][-1], res["ut"][-1], res["w"][-1]
+    gx, gy, gz = O.gradient(uh, res["h"][-1])
+    ex, ey, ez = P.exact_gradient(prob, N)
+    return {
+        ("L2", "u"): O.l2_norm(uh - u), ("Linf", "u"): O.linf_norm(uh - u),
+        ("L2", "grad"): O.grad_l2_norm(gx - ex, gy - ey, gz - ez),
+        ("Linf", "grad"): O.grad_linf_norm(gx - ex, gy - ey, gz - ez),
+        ("L2", "ut"): O.l2_norm(ut - u), ("Linf", "ut"): O.linf_norm(ut - u),
+        ("L2", "w"): O.l2_norm(w - uh), ("Linf", "w"): O.linf_norm(w - uh),
+    }
+
+
+@pytest.mark.parametrize("key,rows", _rows(), ids=lambda v: "-".join(v) if isinstance(v, tuple) else "")
+def test_reproduces_printed_errors(key, rows):
+    name, mesh = key
+    N = tuple(int(v) for v in mesh.split("x"))
+    got = errors_of_run(name, N)
+    for norm, qty, val, src in rows:
+        # three printed significant digits
+        assert got[(norm, qty)] == pytest.approx(val, rel=6e-3), (src, norm, qty)
+
+
+def test_observed_orders_example1():
+    """Fourth order for u_h and grad u_h, sixth for u~_h, fifth for w_h - u_h (Section 5,
+    Tables 1-2; order formula of Section 5)."""
+    e16 = errors_of_run("ex1", (16, 16, 16))
+    e32 = errors_of_run("ex1", (32, 32, 32))
+    order = {k: O.observed_order(e16[k], e32[k]) for k in e16}
+    assert 3.8 < order[("Linf", "u")] < 4.2
+    assert 3.8 < order[("Linf", "grad")] < 4.2
+    assert 5.4 < order[("Linf", "ut")] < 6.2
+    assert 4.7 < order[("Linf", "w")] < 5.3
+
+
+def test_harmonic_example_stops():
+    """Example 2 has f = 0: the stopping test must use the assembled b (Dirichlet lift),
+    else ||f_h|| = 0 and no tolerance is ever met."""
+    N = (16, 16, 16)
+    f, g, _ = P.make_inputs(P.PROBLEMS["ex2"], N)
+    assert np.all(f == 0)
+    res = O.excmg(f, g, (1, 1, 1), N, (4, 4, 4), eps=1e-12, max_iter=500)
+    assert all(it < 500 for it in res["iters"])
+    assert res["relres"][-1] <= 1e-12
+
+
+def test_dense_dsolve_agrees_with_cg_dsolve():
+    N = (16, 16, 16)
+    f, g, _ = P.make_inputs(P.PROBLEMS["ex1"], N)
+    a = O.excmg(f, g, (1, 1, 1), N, (4, 4, 4), eps=1e-13, eps_coarse=1e-14)
+    b = O.excmg(f, g, (1, 1, 1), N, (4, 4, 4), eps=1e-13, dsolve="dense")
+    assert np.max(np.abs(a["u"][1] - b["u"][1])) < 1e-12
+    assert np.max(np.abs(a["u"][-1] - b["u"][-1])) < 1e-11
