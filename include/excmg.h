@@ -1,0 +1,229 @@
+/*
+ * excmg.h -- C ABI of the GB300 (sm_103a) EXCMG solver for the 3D Dirichlet Poisson
+ * problem  u_xx + u_yy + u_zz = f in a box, u = g on its boundary  (Section 1, eq. bvp),
+ * discretised by the 19-point fourth-order compact scheme with unequal meshsizes
+ * (Section 2, eq. compact) and solved by the extrapolation cascadic multigrid method of
+ * Algorithm 1 (Section 3.1).  Reference: Pan, He & Hu, arXiv 1507.05063.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Node arrays.  A grid of Nx x Ny x Nz cells on [0,Lx]x[0,Ly]x[0,Lz] has
+ * (Nx+1)(Ny+1)(Nz+1) nodes (i hx, j hy, k hz), hx = Lx/Nx etc. (Section 2).  Every
+ * node array is float64, dense, x fastest: node (i,j,k) is element
+ * i + (Nx+1)*(j + (Ny+1)*k).  All array pointers are DEVICE pointers, owned by the
+ * caller, at least 8-byte aligned, and must not overlap unless stated.
+ * Levels.  The finest grid is (Nx,Ny,Nz); the coarsest is (Nx0,Ny0,Nz0); every level
+ * halves all three cell counts, so Nx/Nx0 = Ny/Ny0 = Nz/Nz0 = 2^(levels-1) with
+ * levels >= 3, and Nx0, Ny0, Nz0 must be even (the tri-quartic interpolation cells of
+ * Section 3.3 are 2x2x2 coarse elements).  Coarse-level f and g are the finest values
+ * at the coarse nodes.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * Work is enqueued on it; entry points that run CG read convergence flags back and so
+ * return only after their work on the stream has finished.
+ * Workspace.  Scratch memory is caller-owned device memory of at least the size the
+ * matching *_workspace_size query returns, 256-byte aligned.  The library allocates no
+ * device memory.  Calls that share a workspace must not run concurrently.
+ * Errors.  Every entry point returns an excmg_status and never throws.  Invalid
+ * arguments are detected before any work is enqueued.  A CUDA launch or copy error maps
+ * to EXCMG_ERR_CUDA (a sticky error leaves the context unusable, as in CUDA itself).
+ */
+#ifndef EXCMG_H
+#define EXCMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EXCMG_OK = 0,
+  EXCMG_ERR_INVALID_ARG = 1,   /* sizes, pointers, options or alignment rejected */
+  EXCMG_ERR_NOT_CONVERGED = 2, /* a CG loop hit max_iter before its tolerance */
+  EXCMG_ERR_CUDA = 3,          /* a CUDA call failed */
+  EXCMG_ERR_NONFINITE = 4,     /* NaN/Inf met in a CG reduction (e.g. NaN in f or g) */
+  EXCMG_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait ran out */
+  EXCMG_ERR_WORKSPACE = 6      /* workspace NULL, too small or misaligned */
+} excmg_status;
+
+typedef enum {
+  EXCMG_FP64 = 0,  /* CG entirely in float64 */
+  EXCMG_MIXED = 1  /* float32 CG on the correction equation inside float64 iterative
+                      refinement; residuals, reductions, extrapolation in float64 */
+} excmg_precision;
+
+#define EXCMG_MAX_LEVELS 24
+
+/* Box and grids (Section 2: hx = Lx/Nx ...; Algorithm 1: coarsest grid H, L levels). */
+typedef struct {
+  double Lx, Ly, Lz;  /* box lengths, > 0 */
+  int Nx, Ny, Nz;     /* finest-grid cells per direction */
+  int Nx0, Ny0, Nz0;  /* coarsest-grid cells per direction (even) */
+} excmg_grid;
+
+/* Solver options.  Fill with excmg_default_options() and override. */
+typedef struct {
+  int precision;           /* excmg_precision */
+  double eps;              /* relative-residual tolerance on levels >= 2: CG stops when
+                              ||A u - b||_2 <= eps ||b||_2, b the assembled right-hand
+                              side with its Dirichlet lift (Algorithm 1, line 7) */
+  double eps_coarse;       /* same test on levels 0 and 1 (stands in for DSOLVE) */
+  int max_iter;            /* cap on CG iterations per level (per inner solve) */
+  double inner_tol;        /* MIXED: inner float32 CG stops at ||r|| <= inner_tol ||r0|| */
+  int max_refine;          /* MIXED: cap on refinement steps per level */
+  const int* fixed_iters;  /* HOST array of `levels` counts or NULL: run exactly that
+                              many CG iterations on each level (FP64 only; parity tests) */
+  int tile_z;              /* z-slab depth of the stencil kernels; 0 = library default */
+  int chunk;               /* CG iterations enqueued between convergence reads; 0 = auto */
+  int profile;             /* nonzero: time every finest-level CG launch with CUDA events on
+                              the caller's stream (stats.prof_*); adds one event record per
+                              launch */
+} excmg_options;
+
+/* Per-solve statistics, valid when the call returns. */
+typedef struct {
+  int levels;
+  int N[EXCMG_MAX_LEVELS][3];        /* cells per level */
+  int iters[EXCMG_MAX_LEVELS];       /* CG iterations per level (summed over refinements) */
+  int refinements[EXCMG_MAX_LEVELS]; /* MIXED: refinement steps per level */
+  double relres[EXCMG_MAX_LEVELS];   /* final ||r||/||b|| per level (recursive residual
+                                        for FP64; true float64 residual for MIXED) */
+  long long launches;                /* kernels this call launched (all levels) */
+  int prof_steps;                    /* profile: CG steps timed on the finest level */
+  double prof_spmv_ms;               /* profile: summed time of their stencil launches */
+  double prof_update_ms;             /* profile: summed time of their update launches */
+} excmg_stats;
+
+/* Writes the defaults: FP64, eps 1e-9, eps_coarse 1e-12, max_iter 100000,
+   inner_tol 1e-4, max_refine 50, fixed_iters NULL, tile_z 0, chunk 0, profile 0. */
+void excmg_default_options(excmg_options* opt);
+
+/* Human-readable name of a status code (static string). */
+const char* excmg_status_string(excmg_status s);
+
+/* Number of levels of `grid`, or -1 if the grid is invalid. */
+int excmg_num_levels(const excmg_grid* grid);
+
+/* Bytes of workspace excmg_solve needs for `grid` and `opt` (0 if invalid). */
+size_t excmg_workspace_size(const excmg_grid* grid, const excmg_options* opt);
+
+/*
+ * excmg_solve -- Algorithm 1.  Levels 0 and 1: CG from zero (eps_coarse).  Each finer
+ * level: w_h = EXP_finite(u_2h, u_4h) (Section 3.3: eqs. jiedian and zhongdian on the
+ * nodes of grid 2h, tri-quartic Lagrange interpolation eq. inter on every cell of 2x2x2
+ * elements of grid 4h), then CG from w_h (interior) until the relative residual is at
+ * most eps.  On the finest level, optionally u~_h = EXP_true(u_h, u_2h) (eqs. t1,
+ * chenlin; line 10).
+ *   f        [in]  finest-grid node array: the Poisson right-hand side on ALL nodes
+ *                  (the compact RHS uses f at face neighbours, which may be boundary
+ *                  nodes).
+ *   g        [in]  finest-grid node array; only boundary entries are read (Dirichlet
+ *                  data).
+ *   u        [out] finest-grid node array: the FD solution u_h, boundary = g.
+ *   u_tilde  [out] NULL, or a finest-grid node array receiving EXP_true(u_h, u_2h).
+ *   ws, ws_bytes   workspace of at least excmg_workspace_size(grid, opt) bytes.
+ *   stats    [out] NULL or host struct.
+ * Returns EXCMG_ERR_NOT_CONVERGED if any level hit max_iter (u then holds the last
+ * iterate), EXCMG_ERR_NONFINITE if a reduction turned non-finite.
+ */
+excmg_status excmg_solve(const excmg_grid* grid, const double* f, const double* g,
+                         const excmg_options* opt, double* u, double* u_tilde,
+                         void* ws, size_t ws_bytes, excmg_stats* stats, void* stream);
+
+/*
+ * excmg_grad -- gradient of a node array (Section 5, text of Example 1): on x = 0 and
+ * x = Lx the one-sided fourth-order five-point formulas; at interior x-nodes of every
+ * x-line the compact system (1/6, 4/6, 1/6) u_x = (u_{i+1} - u_{i-1}) / (2 hx), solved
+ * by the Thomas algorithm; likewise along y and z.  Needs Nx, Ny, Nz >= 4 (the five-
+ * point formula); Nx0.. are ignored.  ux, uy, uz [out]: node arrays, all nodes.
+ * No workspace: the forward sweep is stored in the outputs.
+ */
+excmg_status excmg_grad(const excmg_grid* grid, const double* u, double* ux, double* uy,
+                        double* uz, void* stream);
+
+/*
+ * excmg_solve_batched -- `nprob` independent problems (each its own grid, f, g) solved by
+ * Algorithm 1 together: each CG step of every active problem runs in ONE launch of the
+ * stencil kernels over the union of all problems' tiles; problems are aligned on their
+ * finest level.  grids[nprob]: host array; f, g, u: host arrays of device pointers.
+ * opt: shared options (fixed_iters must be NULL).  stats: NULL or host array[nprob].
+ * Workspace: excmg_workspace_size_batched().  1 <= nprob <= 128.
+ */
+size_t excmg_workspace_size_batched(int nprob, const excmg_grid* grids,
+                                    const excmg_options* opt);
+excmg_status excmg_solve_batched(int nprob, const excmg_grid* grids,
+                                 const double* const* f, const double* const* g,
+                                 const excmg_options* opt, double* const* u, void* ws,
+                                 size_t ws_bytes, excmg_stats* stats, void* stream);
+
+/*
+ * excmg_adjoint -- gradients of a scalar loss L(u) through the discrete solve
+ * u_I = A^{-1} b(f, g), u_B = g, with A the SPD form of eq. (FD) (A = -(printed LHS)):
+ *   lambda = A^{-1} (dL/du)_I          (CG on the finest grid, tolerance eps, from 0;
+ *                                        A is symmetric so A^T = A)
+ *   dL/df  = -R^T lambda               (R: the 7-point right-hand-side operator
+ *                                        (6 f_c + sum of face f)/2 of eq. compact)
+ *   dL/dg  = LHS_IB^T lambda + dL/du   on boundary nodes (LHS_IB: the boundary columns
+ *                                        of the printed left-hand side), 0 inside.
+ * The paper has no adjoint; this is the exact transpose of the discrete map.
+ *   dLdu [in]: finest node array.  dLdf, dLdg [out]: finest node arrays.
+ *   stats: iters[0], relres[0] of the lambda solve.
+ * Workspace: excmg_workspace_size_adjoint().  MIXED precision refines the lambda solve.
+ */
+size_t excmg_workspace_size_adjoint(const excmg_grid* grid, const excmg_options* opt);
+excmg_status excmg_adjoint(const excmg_grid* grid, const double* dLdu,
+                           const excmg_options* opt, double* dLdf, double* dLdg,
+                           void* ws, size_t ws_bytes, excmg_stats* stats, void* stream);
+
+/* ---- single steps of the path, exported for parity tests and custom drivers ---- */
+
+/*
+ * excmg_exp_finite -- EXP_finite(u_2h, u_4h) of Algorithm 1 line 6 / Section 3.3 onto
+ * grid h = `grid`'s finest level: u2h and u4h are node arrays of the grids with
+ * Nx/2 and Nx/4 cells.  Writes w (node array of grid h) on all nodes; if g is not NULL
+ * the boundary nodes of w are set to g (the CG start), otherwise they keep their
+ * interpolated values.  Needs Nx, Ny, Nz divisible by 8.
+ */
+excmg_status excmg_exp_finite(const excmg_grid* grid, const double* u2h, const double* u4h,
+                              const double* g, double* w, void* stream);
+
+/*
+ * excmg_exp_true -- EXP_true(u_h, u_2h) of Algorithm 1 line 10 (Section 3.3): eq. (t1)
+ * (16 u_h - u_2h)/15 at the nodes of grid 2h, eq. (chenlin) u_h + (d_a + d_b)/30 along
+ * every edge, face diagonal or space diagonal through the other nodes (averaged over the
+ * diagonals), d = u_h - u_2h.  uh: grid h node array; u2h: Nx/2 grid.  Needs Nx, Ny, Nz
+ * even.
+ */
+excmg_status excmg_exp_true(const excmg_grid* grid, const double* uh, const double* u2h,
+                            double* ut, void* stream);
+
+/* Bytes of workspace excmg_cg and excmg_residual need on the grid Nx x Ny x Nz
+   (Nx0.. ignored; each N >= 2); 0 if invalid. */
+size_t excmg_workspace_size_level(const excmg_grid* grid, const excmg_options* opt);
+
+/*
+ * excmg_cg -- CG on the grid Nx x Ny x Nz alone (Algorithm 1 lines 7-9; Nx0.. ignored):
+ * from the interior values of u (boundary entries of u must already hold g) until
+ * ||r|| <= opt->eps ||b|| (or exactly opt->fixed_iters[0] iterations; MIXED refines with
+ * float32 inner solves).  u [in/out].  Workspace: excmg_workspace_size_level().
+ * stats: iters[0], refinements[0], relres[0].
+ */
+excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_options* opt,
+                      double* u, void* ws, size_t ws_bytes, excmg_stats* stats,
+                      void* stream);
+
+/*
+ * excmg_residual -- r = b - A u_I = LHS(u) - RHS(f) at interior nodes (0 on the
+ * boundary), eq. (compact) / (FD), in float64; also returns ||r||_2 and ||b||_2 (b with
+ * its Dirichlet lift taken from u's boundary entries) in *rnorm, *bnorm (host).
+ * Workspace: excmg_workspace_size_level().
+ */
+excmg_status excmg_residual(const excmg_grid* grid, const double* f, const double* u,
+                            double* r, double* rnorm, double* bnorm, void* ws,
+                            size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXCMG_H */

@@ -1,0 +1,907 @@
+// C ABI of libexcmg (include/excmg.h): argument checks, workspace layout, and the host
+// side of Algorithm 1 -- the level loop, the CG loop with its convergence reads, the
+// MIXED iterative refinement, the batched phases and the adjoint.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "excmg_internal.cuh"
+
+namespace excmg {
+
+Grid3 make_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz) {
+  Grid3 g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.sy = nx + 1;
+  g.sz = (long long)(nx + 1) * (ny + 1);
+  g.hx = Lx / nx;
+  g.hy = Ly / ny;
+  g.hz = Lz / nz;
+  return g;
+}
+
+Coef make_coef(const Grid3& g) {
+  const double a = 1.0 / (g.hx * g.hx), b = 1.0 / (g.hy * g.hy), c = 1.0 / (g.hz * g.hz);
+  Coef A;
+  A.c0 = 8.0 * (a + b + c);
+  A.fx = -(4.0 * a - b - c);
+  A.fy = -(4.0 * b - a - c);
+  A.fz = -(4.0 * c - a - b);
+  A.exy = -0.5 * (a + b);
+  A.exz = -0.5 * (a + c);
+  A.eyz = -0.5 * (b + c);
+  return A;
+}
+
+Tiling make_tiling(const Grid3& g, int tz) {
+  Tiling t;
+  t.tz = tz;
+  t.ntx = (g.nx + 1 + kTX - 1) / kTX;
+  t.nty = (g.ny + 1 + kTY - 1) / kTY;
+  t.ntz = (g.nz + 1 + tz - 1) / tz;
+  return t;
+}
+
+// Slab depth: among 4..64 the one minimising (waves of tiles) x (planes staged per tile),
+// a model of the stencil kernel's time when every block runs at the same rate.
+int choose_tz(const Grid3& g, int grid_blocks, int requested) {
+  if (requested > 0) return requested;
+  int best = 16;
+  double best_cost = 1e300;
+  const int cands[] = {4, 6, 8, 12, 16, 24, 32, 48, 64};
+  for (int tz : cands) {
+    const Tiling t = make_tiling(g, tz);
+    const long long tiles = t.count();
+    const long long waves = (tiles + grid_blocks - 1) / grid_blocks;
+    const int depth = std::min(tz, g.nz + 1);
+    const double cost = (double)waves * (depth + 2);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = tz;
+    }
+  }
+  return best;
+}
+
+}  // namespace excmg
+
+using namespace excmg;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Level {
+  int nx, ny, nz;
+  long long nodes() const { return (long long)(nx + 1) * (ny + 1) * (nz + 1); }
+};
+
+// Validated level list of a grid, coarsest first; empty if invalid.
+std::vector<Level> levels_of(const excmg_grid* gr) {
+  std::vector<Level> out;
+  if (!gr) return out;
+  if (!(gr->Lx > 0) || !(gr->Ly > 0) || !(gr->Lz > 0)) return out;
+  if (gr->Nx0 < 2 || gr->Ny0 < 2 || gr->Nz0 < 2) return out;
+  if (gr->Nx0 % 2 || gr->Ny0 % 2 || gr->Nz0 % 2) return out;
+  if (gr->Nx % gr->Nx0 || gr->Ny % gr->Ny0 || gr->Nz % gr->Nz0) return out;
+  const int rx = gr->Nx / gr->Nx0, ry = gr->Ny / gr->Ny0, rz = gr->Nz / gr->Nz0;
+  if (rx != ry || rx != rz || rx < 4 || (rx & (rx - 1))) return out;
+  int lv = 0;
+  while ((1 << lv) < rx) ++lv;
+  if (lv + 1 > EXCMG_MAX_LEVELS) return out;
+  if ((long long)(gr->Nx + 1) * (gr->Ny + 1) * (gr->Nz + 1) > (1LL << 40)) return out;
+  for (int l = 0; l <= lv; ++l) out.push_back({gr->Nx0 << l, gr->Ny0 << l, gr->Nz0 << l});
+  return out;
+}
+
+// The single grid Nx x Ny x Nz (coarsest-grid fields ignored); empty if invalid.
+std::vector<Level> single_level(const excmg_grid* gr) {
+  std::vector<Level> out;
+  if (!gr) return out;
+  if (!(gr->Lx > 0) || !(gr->Ly > 0) || !(gr->Lz > 0)) return out;
+  if (gr->Nx < 2 || gr->Ny < 2 || gr->Nz < 2) return out;
+  if ((long long)(gr->Nx + 1) * (gr->Ny + 1) * (gr->Nz + 1) > (1LL << 40)) return out;
+  out.push_back({gr->Nx, gr->Ny, gr->Nz});
+  return out;
+}
+
+bool options_ok(const excmg_options* o) {
+  if (!o) return false;
+  if (o->precision != EXCMG_FP64 && o->precision != EXCMG_MIXED) return false;
+  if (!(o->eps >= 0) || !(o->eps_coarse >= 0) || o->max_iter < 0) return false;
+  if (o->precision == EXCMG_MIXED && (!(o->inner_tol > 0) || !(o->inner_tol < 1) || o->max_refine < 1))
+    return false;
+  if (o->fixed_iters && o->precision != EXCMG_FP64) return false;
+  if (o->tile_z < 0 || o->tile_z > 256 || o->chunk < 0) return false;
+  return true;
+}
+
+// Per-problem workspace layout.
+struct ProbLayout {
+  size_t coarse_off[EXCMG_MAX_LEVELS];  // u of levels 0 .. L-2 (float64)
+  size_t r, pa, pb, q;                  // float64 CG vectors (finest size)
+  size_t r32, pa32, pb32, q32, e32;     // float32 CG vectors (MIXED)
+  size_t bytes;
+};
+
+ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_vectors) {
+  ProbLayout L;
+  memset(&L, 0, sizeof(L));
+  size_t off = 0;
+  for (size_t l = 0; l + 1 < lv.size(); ++l) {
+    L.coarse_off[l] = off;
+    off = align_up(off + sizeof(double) * lv[l].nodes());
+  }
+  const long long nf = lv.back().nodes();
+  if (!mixed || need_fp64_vectors) {
+    L.r = off;
+    off = align_up(off + sizeof(double) * nf);
+    L.pa = off;
+    off = align_up(off + sizeof(double) * nf);
+    L.pb = off;
+    off = align_up(off + sizeof(double) * nf);
+    L.q = off;
+    off = align_up(off + sizeof(double) * nf);
+  }
+  if (mixed) {
+    L.r32 = off;
+    off = align_up(off + sizeof(float) * nf);
+    L.pa32 = off;
+    off = align_up(off + sizeof(float) * nf);
+    L.pb32 = off;
+    off = align_up(off + sizeof(float) * nf);
+    L.q32 = off;
+    off = align_up(off + sizeof(float) * nf);
+    L.e32 = off;
+    off = align_up(off + sizeof(float) * nf);
+  }
+  L.bytes = off;
+  return L;
+}
+
+// Common header of every workspace: states, counters, partials, descriptor tables.
+struct Header {
+  size_t st, counters, partials, cgd, cgf, resd, prold;
+  size_t bytes;
+};
+
+Header header_layout(int nprob) {
+  Header H;
+  size_t off = 0;
+  H.st = off;
+  off = align_up(off + sizeof(CGState) * nprob);
+  H.counters = off;
+  off = align_up(off + sizeof(unsigned) * nprob);
+  H.partials = off;
+  off = align_up(off + sizeof(double) * 2 * (size_t)nprob * kMaxGrid);
+  H.cgd = off;
+  off = align_up(off + sizeof(CGDesc<double>) * nprob);
+  H.cgf = off;
+  off = align_up(off + sizeof(CGDesc<float>) * nprob);
+  H.resd = off;
+  off = align_up(off + sizeof(ResDesc) * nprob);
+  H.prold = off;
+  off = align_up(off + sizeof(ProlongDesc) * nprob);
+  H.bytes = off;
+  return H;
+}
+
+#define CK(call)                              \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return EXCMG_ERR_CUDA; \
+  } while (0)
+
+// One problem's static data for a solve.
+struct Prob {
+  std::vector<Level> lv;
+  excmg_grid gr;
+  const double* f;
+  const double* g;
+  double* u;             // finest output
+  char* base;            // its workspace region
+  ProbLayout L;
+  double* level_u(int l) {
+    return (l + 1 == (int)lv.size()) ? u : reinterpret_cast<double*>(base + L.coarse_off[l]);
+  }
+  Grid3 grid(int l) const {
+    return make_grid(lv[l].nx, lv[l].ny, lv[l].nz, gr.Lx, gr.Ly, gr.Lz);
+  }
+  View fview(int l) const {
+    const int s = lv.back().nx / lv[l].nx;
+    const Grid3 fg = grid((int)lv.size() - 1);
+    return View{f, s, s * fg.sy, s * fg.sz};
+  }
+  View gview(int l) const {
+    const int s = lv.back().nx / lv[l].nx;
+    const Grid3 fg = grid((int)lv.size() - 1);
+    return View{g, s, s * fg.sy, s * fg.sz};
+  }
+};
+
+// Event timing of the finest-level CG launches (options.profile).
+struct Prof {
+  std::vector<cudaEvent_t> pool;
+  int steps = 0;
+  double spmv_ms = 0.0, update_ms = 0.0;
+  ~Prof() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+  cudaEvent_t get(size_t i) {
+    while (pool.size() <= i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[i];
+  }
+};
+
+struct Ctx {
+  char* ws;
+  Header H;
+  cudaStream_t s;
+  long long* launches = nullptr;  // kernels launched by this call
+  Prof* prof = nullptr;           // set while the finest level of a profiled call runs
+  CGState* st() const { return reinterpret_cast<CGState*>(ws + H.st); }
+  unsigned* counters() const { return reinterpret_cast<unsigned*>(ws + H.counters); }
+  double* partials() const { return reinterpret_cast<double*>(ws + H.partials); }
+  CGDesc<double>* cgd() const { return reinterpret_cast<CGDesc<double>*>(ws + H.cgd); }
+  CGDesc<float>* cgf() const { return reinterpret_cast<CGDesc<float>*>(ws + H.cgf); }
+  ResDesc* resd() const { return reinterpret_cast<ResDesc*>(ws + H.resd); }
+  ProlongDesc* prold() const { return reinterpret_cast<ProlongDesc*>(ws + H.prold); }
+};
+
+excmg_status read_states(const Ctx& c, int nprob, std::vector<CGState>& hs) {
+  hs.resize(nprob);
+  CK(cudaMemcpyAsync(hs.data(), c.st(), sizeof(CGState) * nprob, cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  return EXCMG_OK;
+}
+
+// Runs CG steps over the problems described by `descs` (device copy, `n` entries) until
+// every one of them is done.  Returns the number of convergence reads.
+template <typename T>
+excmg_status cg_loop(const Ctx& c, int n, const CGDesc<T>* ddesc, long long tiles, int grid,
+                     const std::vector<int>& slots, int nslots, int chunk0,
+                     std::vector<CGState>& hs) {
+  int chunk = chunk0 > 0 ? chunk0 : 4;
+  Prof* prof = (c.prof && n == 1) ? c.prof : nullptr;
+  int launched = 0;
+  for (;;) {
+    for (int m = 0; m < chunk; ++m) {
+      if (prof) {
+        const size_t b = 3 * (size_t)launched;
+        cudaEvent_t e0 = prof->get(b), e1 = prof->get(b + 1), e2 = prof->get(b + 2);
+        CK(launch_cg_step<T>(n, ddesc, tiles, grid, c.st(), c.partials(), c.counters(), c.s, e0,
+                             e1, e2));
+      } else {
+        CK(launch_cg_step<T>(n, ddesc, tiles, grid, c.st(), c.partials(), c.counters(), c.s));
+      }
+      ++launched;
+      if (c.launches) *c.launches += 2;
+    }
+    excmg_status e = read_states(c, nslots, hs);
+    if (e != EXCMG_OK) return e;
+    bool all = true;
+    for (int sl : slots) all = all && hs[sl].done;
+    if (all) break;
+    if (chunk0 <= 0) chunk = std::min(chunk * 2, 64);
+  }
+  if (prof) {
+    // steps after convergence returned at once; time only the steps that ran
+    const int real = std::min(hs[slots[0]].iter, launched);
+    for (int k = 0; k < real; ++k) {
+      float a = 0.f, b = 0.f;
+      CK(cudaEventElapsedTime(&a, prof->pool[3 * k], prof->pool[3 * k + 1]));
+      CK(cudaEventElapsedTime(&b, prof->pool[3 * k + 1], prof->pool[3 * k + 2]));
+      prof->spmv_ms += a;
+      prof->update_ms += b;
+    }
+    prof->steps += real;
+  }
+  return EXCMG_OK;
+}
+
+int tiles_grid(long long tiles) { return persistent_grid(tiles); }
+
+// One linear system A x = b of a solve phase: its residual descriptor (b from f and the
+// Dirichlet data in x's boundary, or from `src`), its float64 CG descriptor and its
+// float32 correction descriptor (MIXED).
+struct Item {
+  ResDesc res;
+  CGDesc<double> d64;
+  CGDesc<float> d32;
+  double eps;           // stop at ||r|| <= eps ||b||
+  long long nodes;
+  // results
+  int iters, refs, status;
+  double relres;
+};
+
+ResDesc make_res(const Grid3& g, const Tiling& t, int slot, const double* x, View f,
+                 const double* src) {
+  ResDesc r;
+  memset(&r, 0, sizeof(r));
+  r.g = g;
+  r.A = make_coef(g);
+  r.t = t;
+  r.slot = slot;
+  r.u = x;
+  r.f = f;
+  r.src = src;
+  r.want_b = 1;
+  return r;
+}
+
+// FP64: residual, then CG<double> until ||r|| <= eps ||b|| (fixed counts when
+// `fixed` is given).  MIXED: iterative refinement -- float64 residual r, float32 CG on
+// A e = r from e = 0 to inner_tol, x += e -- until ||r|| <= eps ||b||.
+excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_options* o,
+                         int nslots, const int* fixed) {
+  const bool mixed = o->precision == EXCMG_MIXED;
+  const int n = (int)items.size();
+  std::vector<CGState> hs;
+  std::vector<ResDesc> hr;
+  long long tiles = 0;
+  for (int a = 0; a < n; ++a) {
+    Item& it = items[a];
+    it.iters = it.refs = 0;
+    it.status = EXCMG_OK;
+    it.relres = 0.0;
+    ResDesc r = it.res;
+    r.tile_begin = tiles;
+    it.d64.tile_begin = tiles;
+    it.d32.tile_begin = tiles;
+    tiles += r.t.count();
+    if (mixed) {
+      r.r = it.d32.r;
+      r.tol_b2 = 0.0;
+      r.tol_r2 = o->inner_tol * o->inner_tol;
+      r.fixed = 0;
+      r.max_iter = o->max_iter;
+    } else {
+      r.r = it.d64.r;
+      r.tol_b2 = it.eps * it.eps;
+      r.tol_r2 = 0.0;
+      r.fixed = fixed ? 1 : 0;
+      r.max_iter = fixed ? fixed[a] : o->max_iter;
+    }
+    it.res = r;
+    hr.push_back(r);
+  }
+  if (n == 0) return EXCMG_OK;
+  if (!mixed) {
+    std::vector<CGDesc<double>> hd;
+    std::vector<int> slots;
+    for (auto& it : items) {
+      hd.push_back(it.d64);
+      slots.push_back(it.d64.slot);
+    }
+    const int grid = tiles_grid(tiles);
+    CK(cudaMemcpyAsync(c.resd(), hr.data(), sizeof(ResDesc) * n, cudaMemcpyHostToDevice, c.s));
+    CK(cudaMemcpyAsync(c.cgd(), hd.data(), sizeof(CGDesc<double>) * n, cudaMemcpyHostToDevice, c.s));
+    CK(launch_residual(false, n, c.resd(), tiles, grid, c.st(), c.partials(), c.counters(), c.s));
+    if (c.launches) *c.launches += 1;
+    excmg_status e = cg_loop<double>(c, n, c.cgd(), tiles, grid, slots, nslots, o->chunk, hs);
+    if (e != EXCMG_OK) return e;
+    for (auto& it : items) {
+      const CGState& S = hs[it.d64.slot];
+      it.iters = S.iter;
+      it.relres = S.bb > 0 ? sqrt(S.rr / S.bb) : 0.0;
+      it.status = S.status;
+    }
+    return EXCMG_OK;
+  }
+  for (auto& it : items)
+    CK(cudaMemsetAsync(it.d32.x, 0, sizeof(float) * it.nodes, c.s));
+  std::vector<int> cur(n);
+  for (int a = 0; a < n; ++a) cur[a] = a;
+  for (;;) {
+    std::vector<ResDesc> rr;
+    long long rt = 0;
+    for (int a : cur) {
+      ResDesc r = items[a].res;
+      r.tile_begin = rt;
+      rt += r.t.count();
+      rr.push_back(r);
+    }
+    const int nr = (int)rr.size();
+    CK(cudaMemcpyAsync(c.resd(), rr.data(), sizeof(ResDesc) * nr, cudaMemcpyHostToDevice, c.s));
+    CK(launch_residual(true, nr, c.resd(), rt, tiles_grid(rt), c.st(), c.partials(), c.counters(), c.s));
+    if (c.launches) *c.launches += 1;
+    excmg_status e = read_states(c, nslots, hs);
+    if (e != EXCMG_OK) return e;
+    std::vector<int> next;
+    for (int a : cur) {
+      Item& it = items[a];
+      const CGState& S = hs[it.d32.slot];
+      it.relres = S.bb > 0 ? sqrt(S.rr / S.bb) : 0.0;
+      if (S.status != EXCMG_OK) {
+        it.status = S.status;
+      } else if (!(S.rr <= it.eps * it.eps * S.bb)) {
+        if (it.refs >= o->max_refine)
+          it.status = EXCMG_ERR_NOT_CONVERGED;
+        else
+          next.push_back(a);
+      }
+    }
+    if (next.empty()) return EXCMG_OK;
+    std::vector<CGDesc<float>> fd;
+    std::vector<int> fslots;
+    long long ft = 0;
+    for (int a : next) {
+      CGDesc<float> d = items[a].d32;
+      d.tile_begin = ft;
+      ft += d.t.count();
+      fd.push_back(d);
+      fslots.push_back(d.slot);
+    }
+    const int nf = (int)fd.size();
+    const int fgrid = tiles_grid(ft);
+    CK(cudaMemcpyAsync(c.cgf(), fd.data(), sizeof(CGDesc<float>) * nf, cudaMemcpyHostToDevice, c.s));
+    e = cg_loop<float>(c, nf, c.cgf(), ft, fgrid, fslots, nslots, o->chunk, hs);
+    if (e != EXCMG_OK) return e;
+    for (int a : next) {
+      items[a].iters += hs[items[a].d32.slot].iter;
+      items[a].refs += 1;
+      // an inner solve that hits max_iter is not fatal: refinement continues
+    }
+    CK(launch_add_correction(nf, c.cgf(), ft, fgrid, c.s));
+    if (c.launches) *c.launches += 1;
+    cur = next;
+  }
+}
+
+Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
+  const Grid3 g = p.grid(l);
+  const int tz = choose_tz(g, persistent_grid(1LL << 40), o->tile_z);
+  const Tiling t = make_tiling(g, tz);
+  Item it;
+  memset(&it, 0, sizeof(it));
+  it.eps = (l < 2) ? o->eps_coarse : o->eps;
+  it.nodes = g.nodes();
+  it.res = make_res(g, t, slot, p.level_u(l), p.fview(l), nullptr);
+  CGDesc<double>& d = it.d64;
+  d.g = g;
+  d.A = it.res.A;
+  d.t = t;
+  d.slot = slot;
+  d.x = p.level_u(l);
+  d.r = reinterpret_cast<double*>(p.base + p.L.r);
+  d.pa = reinterpret_cast<double*>(p.base + p.L.pa);
+  d.pb = reinterpret_cast<double*>(p.base + p.L.pb);
+  d.q = reinterpret_cast<double*>(p.base + p.L.q);
+  d.aux = nullptr;
+  CGDesc<float>& f = it.d32;
+  f.g = g;
+  f.A = it.res.A;
+  f.t = t;
+  f.slot = slot;
+  f.x = reinterpret_cast<float*>(p.base + p.L.e32);
+  f.r = reinterpret_cast<float*>(p.base + p.L.r32);
+  f.pa = reinterpret_cast<float*>(p.base + p.L.pa32);
+  f.pb = reinterpret_cast<float*>(p.base + p.L.pb32);
+  f.q = reinterpret_cast<float*>(p.base + p.L.q32);
+  f.aux = p.level_u(l);
+  return it;
+}
+
+// The level loop of Algorithm 1 for one or more problems (a single solve is nprob = 1).
+// Problems are aligned on their finest level: in phase s, problem i works on level
+// s - (maxL - L_i).
+excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_tilde,
+                       excmg_stats* stats, const Ctx& c0) {
+  const int np = (int)P.size();
+  long long launches = 0;
+  Ctx c = c0;
+  c.launches = &launches;
+  struct Report {
+    excmg_stats* st;
+    long long* n;
+    ~Report() {
+      if (st) st[0].launches = *n;
+    }
+  } report{stats, &launches};
+  int maxL = 0;
+  for (auto& p : P) maxL = std::max(maxL, (int)p.lv.size());
+  CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned) * np, c.s));
+  excmg_status result = EXCMG_OK;
+  if (stats) {
+    for (int i = 0; i < np; ++i) {
+      memset(&stats[i], 0, sizeof(excmg_stats));
+      stats[i].levels = (int)P[i].lv.size();
+      for (int l = 0; l < stats[i].levels; ++l) {
+        stats[i].N[l][0] = P[i].lv[l].nx;
+        stats[i].N[l][1] = P[i].lv[l].ny;
+        stats[i].N[l][2] = P[i].lv[l].nz;
+      }
+    }
+  }
+  std::vector<ProlongDesc> hp(np);
+  for (int phase = 0; phase < maxL; ++phase) {
+    std::vector<int> act, lev;
+    for (int i = 0; i < np; ++i) {
+      const int l = phase - (maxL - (int)P[i].lv.size());
+      if (l >= 0) {
+        act.push_back(i);
+        lev.push_back(l);
+      }
+    }
+    const int na = (int)act.size();
+    // 1. initial guess: zero inside (levels 0, 1) or w_h = EXP_finite(u_2h, u_4h)
+    int npro = 0;
+    long long pblocks = 0;
+    for (int a = 0; a < na; ++a) {
+      Prob& p = P[act[a]];
+      const int l = lev[a];
+      const Grid3 g = p.grid(l);
+      if (l < 2) {
+        CK(launch_boundary_init(g, p.gview(l), p.level_u(l), c.s));
+        if (c.launches) *c.launches += 1;
+      } else {
+        ProlongDesc d;
+        d.g = g;
+        d.u2h = p.level_u(l - 1);
+        d.u4h = p.level_u(l - 2);
+        d.gb = p.gview(l);
+        d.w = p.level_u(l);
+        d.nbx = (g.nx + 31) / 32;
+        d.nby = g.ny / 8;
+        d.nbz = g.nz / 8;
+        d.block_begin = pblocks;
+        pblocks += (long long)d.nbx * d.nby * d.nbz;
+        hp[npro++] = d;
+      }
+    }
+    if (npro > 0) {
+      CK(cudaMemcpyAsync(c.prold(), hp.data(), sizeof(ProlongDesc) * npro, cudaMemcpyHostToDevice, c.s));
+      CK(launch_exp_finite(npro, c.prold(), pblocks, c.s));
+      if (c.launches) *c.launches += 1;
+    }
+    // 2. CG (FP64) or refinement (MIXED) on every active problem's level
+    std::vector<Item> items;
+    std::vector<int> fixed;
+    for (int a = 0; a < na; ++a) {
+      items.push_back(make_item(P[act[a]], lev[a], act[a], o));
+      if (o->fixed_iters) fixed.push_back(o->fixed_iters[lev[a]]);
+    }
+    Ctx cc = c;
+    Prof prof;
+    if (o->profile && np == 1 && phase == maxL - 1) cc.prof = &prof;
+    excmg_status e = solve_items(cc, items, o, np, o->fixed_iters ? fixed.data() : nullptr);
+    if (e != EXCMG_OK) return e;
+    if (cc.prof && stats) {
+      stats[0].prof_steps = prof.steps;
+      stats[0].prof_spmv_ms = prof.spmv_ms;
+      stats[0].prof_update_ms = prof.update_ms;
+    }
+    for (int a = 0; a < na; ++a) {
+      const Item& it = items[a];
+      if (stats) {
+        stats[act[a]].iters[lev[a]] = it.iters;
+        stats[act[a]].refinements[lev[a]] = it.refs;
+        stats[act[a]].relres[lev[a]] = it.relres;
+      }
+      if (it.status != EXCMG_OK && result == EXCMG_OK) result = (excmg_status)it.status;
+    }
+    if (result == EXCMG_ERR_NONFINITE) return result;
+  }
+  if (u_tilde && np == 1) {
+    Prob& p = P[0];
+    const int l = (int)p.lv.size() - 1;
+    CK(launch_exp_true(p.grid(l), p.level_u(l), p.level_u(l - 1), u_tilde, c.s));
+    if (c.launches) *c.launches += 1;
+  }
+  CK(cudaStreamSynchronize(c.s));
+  CK(cudaGetLastError());
+  return result;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+void excmg_default_options(excmg_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = EXCMG_FP64;
+  o->eps = 1e-9;
+  o->eps_coarse = 1e-12;
+  o->max_iter = 100000;
+  o->inner_tol = 1e-4;
+  o->max_refine = 50;
+  o->fixed_iters = nullptr;
+  o->tile_z = 0;
+  o->chunk = 0;
+  o->profile = 0;
+}
+
+const char* excmg_status_string(excmg_status s) {
+  switch (s) {
+    case EXCMG_OK: return "EXCMG_OK";
+    case EXCMG_ERR_INVALID_ARG: return "EXCMG_ERR_INVALID_ARG";
+    case EXCMG_ERR_NOT_CONVERGED: return "EXCMG_ERR_NOT_CONVERGED";
+    case EXCMG_ERR_CUDA: return "EXCMG_ERR_CUDA";
+    case EXCMG_ERR_NONFINITE: return "EXCMG_ERR_NONFINITE";
+    case EXCMG_ERR_TIMEOUT: return "EXCMG_ERR_TIMEOUT";
+    case EXCMG_ERR_WORKSPACE: return "EXCMG_ERR_WORKSPACE";
+  }
+  return "EXCMG_UNKNOWN_STATUS";
+}
+
+int excmg_num_levels(const excmg_grid* grid) {
+  const auto lv = levels_of(grid);
+  return lv.empty() ? -1 : (int)lv.size();
+}
+
+size_t excmg_workspace_size(const excmg_grid* grid, const excmg_options* opt) {
+  const auto lv = levels_of(grid);
+  if (lv.empty() || !options_ok(opt)) return 0;
+  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false).bytes;
+}
+
+size_t excmg_workspace_size_batched(int nprob, const excmg_grid* grids, const excmg_options* opt) {
+  if (nprob < 1 || nprob > kMaxProb || !grids || !options_ok(opt) || opt->fixed_iters) return 0;
+  size_t total = header_layout(nprob).bytes;
+  for (int i = 0; i < nprob; ++i) {
+    const auto lv = levels_of(&grids[i]);
+    if (lv.empty()) return 0;
+    total += prob_layout(lv, opt->precision == EXCMG_MIXED, false).bytes;
+  }
+  return total;
+}
+
+excmg_status excmg_solve(const excmg_grid* grid, const double* f, const double* g,
+                         const excmg_options* opt, double* u, double* u_tilde, void* ws,
+                         size_t ws_bytes, excmg_stats* stats, void* stream) {
+  const auto lv = levels_of(grid);
+  if (lv.empty() || !options_ok(opt) || !f || !g || !u) return EXCMG_ERR_INVALID_ARG;
+  if (!aligned(f, 8) || !aligned(g, 8) || !aligned(u, 8) || (u_tilde && !aligned(u_tilde, 8)))
+    return EXCMG_ERR_INVALID_ARG;
+  if (u == f || u == g || (u_tilde && (u_tilde == u || u_tilde == f || u_tilde == g)))
+    return EXCMG_ERR_INVALID_ARG;
+  if (opt->fixed_iters)
+    for (size_t l = 0; l < lv.size(); ++l)
+      if (opt->fixed_iters[l] < 0) return EXCMG_ERR_INVALID_ARG;
+  const size_t need = excmg_workspace_size(grid, opt);
+  if (!ws || ws_bytes < need || !aligned(ws, kAlign)) return EXCMG_ERR_WORKSPACE;
+  Ctx c;
+  c.ws = static_cast<char*>(ws);
+  c.H = header_layout(1);
+  c.s = static_cast<cudaStream_t>(stream);
+  std::vector<Prob> P(1);
+  P[0].lv = lv;
+  P[0].gr = *grid;
+  P[0].f = f;
+  P[0].g = g;
+  P[0].u = u;
+  P[0].base = c.ws + c.H.bytes;
+  P[0].L = prob_layout(lv, opt->precision == EXCMG_MIXED, false);
+  return run_excmg(P, opt, u_tilde, stats, c);
+}
+
+excmg_status excmg_solve_batched(int nprob, const excmg_grid* grids, const double* const* f,
+                                 const double* const* g, const excmg_options* opt,
+                                 double* const* u, void* ws, size_t ws_bytes,
+                                 excmg_stats* stats, void* stream) {
+  if (nprob < 1 || nprob > kMaxProb || !grids || !f || !g || !u || !options_ok(opt) ||
+      opt->fixed_iters)
+    return EXCMG_ERR_INVALID_ARG;
+  const size_t need = excmg_workspace_size_batched(nprob, grids, opt);
+  if (need == 0) return EXCMG_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < need || !aligned(ws, kAlign)) return EXCMG_ERR_WORKSPACE;
+  Ctx c;
+  c.ws = static_cast<char*>(ws);
+  c.H = header_layout(nprob);
+  c.s = static_cast<cudaStream_t>(stream);
+  std::vector<Prob> P(nprob);
+  char* base = c.ws + c.H.bytes;
+  for (int i = 0; i < nprob; ++i) {
+    P[i].lv = levels_of(&grids[i]);
+    if (!f[i] || !g[i] || !u[i] || !aligned(f[i], 8) || !aligned(g[i], 8) || !aligned(u[i], 8))
+      return EXCMG_ERR_INVALID_ARG;
+    P[i].gr = grids[i];
+    P[i].f = f[i];
+    P[i].g = g[i];
+    P[i].u = u[i];
+    P[i].base = base;
+    P[i].L = prob_layout(P[i].lv, opt->precision == EXCMG_MIXED, false);
+    base += P[i].L.bytes;
+  }
+  return run_excmg(P, opt, nullptr, stats, c);
+}
+
+excmg_status excmg_exp_finite(const excmg_grid* grid, const double* u2h, const double* u4h,
+                              const double* g, double* w, void* stream) {
+  if (!grid || !u2h || !u4h || !w) return EXCMG_ERR_INVALID_ARG;
+  if (grid->Nx % 8 || grid->Ny % 8 || grid->Nz % 8 || grid->Nx < 8 || grid->Ny < 8 || grid->Nz < 8)
+    return EXCMG_ERR_INVALID_ARG;
+  if (!(grid->Lx > 0) || !(grid->Ly > 0) || !(grid->Lz > 0)) return EXCMG_ERR_INVALID_ARG;
+  const Grid3 gg = make_grid(grid->Nx, grid->Ny, grid->Nz, grid->Lx, grid->Ly, grid->Lz);
+  ProlongDesc d;
+  d.g = gg;
+  d.u2h = u2h;
+  d.u4h = u4h;
+  d.gb = View{g, 1, gg.sy, gg.sz};  // p == NULL: keep the interpolated boundary
+  d.w = w;
+  d.nbx = (gg.nx + 31) / 32;
+  d.nby = gg.ny / 8;
+  d.nbz = gg.nz / 8;
+  d.block_begin = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(launch_exp_finite_one(d, s));
+  CK(cudaStreamSynchronize(s));
+  return EXCMG_OK;
+}
+
+excmg_status excmg_exp_true(const excmg_grid* grid, const double* uh, const double* u2h,
+                            double* ut, void* stream) {
+  if (!grid || !uh || !u2h || !ut) return EXCMG_ERR_INVALID_ARG;
+  if (grid->Nx % 2 || grid->Ny % 2 || grid->Nz % 2 || grid->Nx < 2 || grid->Ny < 2 || grid->Nz < 2)
+    return EXCMG_ERR_INVALID_ARG;
+  if (!(grid->Lx > 0) || !(grid->Ly > 0) || !(grid->Lz > 0)) return EXCMG_ERR_INVALID_ARG;
+  const Grid3 gg = make_grid(grid->Nx, grid->Ny, grid->Nz, grid->Lx, grid->Ly, grid->Lz);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(launch_exp_true(gg, uh, u2h, ut, s));
+  CK(cudaStreamSynchronize(s));
+  return EXCMG_OK;
+}
+
+excmg_status excmg_grad(const excmg_grid* grid, const double* u, double* ux, double* uy,
+                        double* uz, void* stream) {
+  if (!grid || !u || !ux || !uy || !uz) return EXCMG_ERR_INVALID_ARG;
+  if (grid->Nx < 4 || grid->Ny < 4 || grid->Nz < 4) return EXCMG_ERR_INVALID_ARG;
+  if (!(grid->Lx > 0) || !(grid->Ly > 0) || !(grid->Lz > 0)) return EXCMG_ERR_INVALID_ARG;
+  if (ux == u || uy == u || uz == u || ux == uy || ux == uz || uy == uz) return EXCMG_ERR_INVALID_ARG;
+  const Grid3 gg = make_grid(grid->Nx, grid->Ny, grid->Nz, grid->Lx, grid->Ly, grid->Lz);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(launch_grad(gg, u, ux, uy, uz, s));
+  CK(cudaStreamSynchronize(s));
+  return EXCMG_OK;
+}
+
+size_t excmg_workspace_size_level(const excmg_grid* grid, const excmg_options* opt) {
+  const auto lv = single_level(grid);
+  if (lv.empty() || !options_ok(opt)) return 0;
+  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false).bytes;
+}
+
+excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_options* opt,
+                      double* u, void* ws, size_t ws_bytes, excmg_stats* stats, void* stream) {
+  const auto lv = single_level(grid);
+  if (lv.empty() || !options_ok(opt) || !f || !u || u == f) return EXCMG_ERR_INVALID_ARG;
+  if (opt->fixed_iters && opt->fixed_iters[0] < 0) return EXCMG_ERR_INVALID_ARG;
+  const size_t need = excmg_workspace_size_level(grid, opt);
+  if (!ws || ws_bytes < need || !aligned(ws, kAlign)) return EXCMG_ERR_WORKSPACE;
+  Ctx c;
+  c.ws = static_cast<char*>(ws);
+  c.H = header_layout(1);
+  c.s = static_cast<cudaStream_t>(stream);
+  Prob p;
+  p.lv = lv;
+  p.gr = *grid;
+  p.f = f;
+  p.g = u;
+  p.u = u;
+  p.base = c.ws + c.H.bytes;
+  p.L = prob_layout(lv, opt->precision == EXCMG_MIXED, false);
+  const int l = (int)lv.size() - 1;
+  std::vector<Item> items{make_item(p, l, 0, opt)};
+  items[0].eps = opt->eps;
+  CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
+  excmg_status e = solve_items(c, items, opt, 1, opt->fixed_iters);
+  if (e != EXCMG_OK) return e;
+  CK(cudaStreamSynchronize(c.s));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->levels = 1;
+    stats->N[0][0] = lv[l].nx;
+    stats->N[0][1] = lv[l].ny;
+    stats->N[0][2] = lv[l].nz;
+    stats->iters[0] = items[0].iters;
+    stats->refinements[0] = items[0].refs;
+    stats->relres[0] = items[0].relres;
+  }
+  return (excmg_status)items[0].status;
+}
+
+excmg_status excmg_residual(const excmg_grid* grid, const double* f, const double* u, double* r,
+                            double* rnorm, double* bnorm, void* ws, size_t ws_bytes,
+                            void* stream) {
+  const auto lv = single_level(grid);
+  if (lv.empty() || !f || !u || !r || r == u || r == f) return EXCMG_ERR_INVALID_ARG;
+  excmg_options o;
+  excmg_default_options(&o);
+  const size_t need = excmg_workspace_size_level(grid, &o);
+  if (!ws || ws_bytes < need || !aligned(ws, kAlign)) return EXCMG_ERR_WORKSPACE;
+  Ctx c;
+  c.ws = static_cast<char*>(ws);
+  c.H = header_layout(1);
+  c.s = static_cast<cudaStream_t>(stream);
+  const Grid3 g = make_grid(grid->Nx, grid->Ny, grid->Nz, grid->Lx, grid->Ly, grid->Lz);
+  const Tiling t = make_tiling(g, choose_tz(g, persistent_grid(1LL << 40), 0));
+  ResDesc d = make_res(g, t, 0, u, View{f, 1, g.sy, g.sz}, nullptr);
+  d.r = r;
+  CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
+  CK(cudaMemcpyAsync(c.resd(), &d, sizeof(d), cudaMemcpyHostToDevice, c.s));
+  CK(launch_residual(false, 1, c.resd(), t.count(), persistent_grid(t.count()), c.st(), c.partials(),
+                     c.counters(), c.s));
+  std::vector<CGState> hs;
+  excmg_status e = read_states(c, 1, hs);
+  if (e != EXCMG_OK) return e;
+  if (rnorm) *rnorm = sqrt(hs[0].rr);
+  if (bnorm) *bnorm = sqrt(hs[0].bb);
+  return EXCMG_OK;
+}
+
+size_t excmg_workspace_size_adjoint(const excmg_grid* grid, const excmg_options* opt) {
+  if (!grid || !options_ok(opt) || opt->fixed_iters) return 0;
+  if (grid->Nx < 2 || grid->Ny < 2 || grid->Nz < 2) return 0;
+  if (!(grid->Lx > 0) || !(grid->Ly > 0) || !(grid->Lz > 0)) return 0;
+  const long long nf = (long long)(grid->Nx + 1) * (grid->Ny + 1) * (grid->Nz + 1);
+  std::vector<Level> lv{{grid->Nx, grid->Ny, grid->Nz}};
+  // lambda (float64) + the CG vectors of one level
+  return header_layout(1).bytes + align_up(sizeof(double) * nf) +
+         prob_layout(lv, opt->precision == EXCMG_MIXED, false).bytes;
+}
+
+excmg_status excmg_adjoint(const excmg_grid* grid, const double* dLdu, const excmg_options* opt,
+                           double* dLdf, double* dLdg, void* ws, size_t ws_bytes,
+                           excmg_stats* stats, void* stream) {
+  if (!grid || !dLdu || !dLdf || !dLdg || !options_ok(opt) || opt->fixed_iters)
+    return EXCMG_ERR_INVALID_ARG;
+  if (dLdf == dLdg || dLdf == dLdu || dLdg == dLdu) return EXCMG_ERR_INVALID_ARG;
+  const size_t need = excmg_workspace_size_adjoint(grid, opt);
+  if (need == 0) return EXCMG_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < need || !aligned(ws, kAlign)) return EXCMG_ERR_WORKSPACE;
+  Ctx c;
+  c.ws = static_cast<char*>(ws);
+  c.H = header_layout(1);
+  c.s = static_cast<cudaStream_t>(stream);
+  const Grid3 g = make_grid(grid->Nx, grid->Ny, grid->Nz, grid->Lx, grid->Ly, grid->Lz);
+  const long long nf = g.nodes();
+  // lambda lives in front of the level vectors; it starts at zero (zero boundary too)
+  double* lam = reinterpret_cast<double*>(c.ws + c.H.bytes);
+  Prob p;
+  p.lv = std::vector<Level>{{grid->Nx, grid->Ny, grid->Nz}};
+  p.gr = *grid;
+  p.f = nullptr;
+  p.g = nullptr;
+  p.u = lam;
+  p.base = c.ws + c.H.bytes + align_up(sizeof(double) * nf);
+  p.L = prob_layout(p.lv, opt->precision == EXCMG_MIXED, false);
+  CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
+  CK(cudaMemsetAsync(lam, 0, sizeof(double) * nf, c.s));
+  Item it = make_item(p, 0, 0, opt);
+  it.eps = opt->eps;
+  // b = s = (dL/du) on interior nodes: r = LHS(lambda) + s = s - A lambda
+  it.res.f = View{nullptr, 0, 0, 0};
+  it.res.src = dLdu;
+  std::vector<Item> items{it};
+  excmg_status e = solve_items(c, items, opt, 1, nullptr);
+  if (e != EXCMG_OK) return e;
+  CK(launch_adjoint_finish(g, it.res.A, lam, dLdu, dLdf, dLdg, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->levels = 1;
+    stats->N[0][0] = g.nx;
+    stats->N[0][1] = g.ny;
+    stats->N[0][2] = g.nz;
+    stats->iters[0] = items[0].iters;
+    stats->refinements[0] = items[0].refs;
+    stats->relres[0] = items[0].relres;
+  }
+  return (excmg_status)items[0].status;
+}
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// Internal declarations shared by the CUDA translation units of libexcmg.
+//
+// Data layout: every level's node array is dense float64 (or float32 for the inner
+// correction solve of MIXED mode), x fastest, node (i,j,k) at i + sy*j + sz*k with
+// sy = nx+1, sz = (nx+1)(ny+1).  Arrays used by CG (x, r, p, q) hold zeros on boundary
+// nodes except x, whose boundary holds the Dirichlet data g: the stencil applied to p
+// with zero boundary is exactly A p on the interior unknowns (Section 2, eq. FD).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "excmg.h"
+
+namespace excmg {
+
+constexpr int kMaxProb = 128;    // problems per batched launch
+constexpr int kThreads = 256;    // threads of every tiled kernel
+constexpr int kTX = 32;          // x-width of a stencil tile (one warp)
+constexpr int kTY = 8;           // y-rows of a stencil tile
+constexpr int kMaxGrid = 4096;   // cap on persistent grid size (partials per problem)
+
+struct Grid3 {
+  int nx, ny, nz;      // cells per direction
+  long long sy, sz;    // node strides
+  double hx, hy, hz;   // meshsizes
+  __host__ __device__ long long nodes() const { return sz * (long long)(nz + 1); }
+};
+
+Grid3 make_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz);
+
+// Weights of A = -(printed left-hand side of eq. compact).  a = 1/hx^2 ...
+// centre 8(a+b+c); x-faces -(4a-b-c); y-faces -(4b-a-c); z-faces -(4c-a-b);
+// xy-edges -(a+b)/2; xz-edges -(a+c)/2; yz-edges -(b+c)/2.
+struct Coef {
+  double c0, fx, fy, fz, exy, exz, eyz;
+};
+Coef make_coef(const Grid3& g);
+
+// A finest-grid node array seen at the nodes of a coarser level (injection).
+struct View {
+  const double* p;
+  long long sx, sy, sz;
+  __device__ __forceinline__ double at(long long i, long long j, long long k) const {
+    return p[i * sx + j * sy + k * sz];
+  }
+};
+
+// CG scalars of one problem, resident in device memory (workspace).
+struct CGState {
+  double rr;      // r.r of the current residual
+  double pq;      // p.Ap of the current step
+  double alpha, beta;
+  double tol2;    // stop when rr <= tol2
+  double bb;      // ||b||^2 of the level
+  double rr0;     // rr when the loop started
+  int iter, max_iter;
+  int done;       // 1: no further CG work for this problem
+  int first;      // 1: next step sets p = r
+  int status;     // excmg_status
+  int fixed;      // 1: max_iter is an exact count, reaching it is not an error
+};
+
+// Tiling of one problem's node box for the stencil and vector kernels: tiles of
+// kTX x kTY columns and tz planes.
+struct Tiling {
+  int ntx, nty, ntz, tz;
+  __host__ __device__ long long count() const { return (long long)ntx * nty * ntz; }
+};
+Tiling make_tiling(const Grid3& g, int tz);
+int choose_tz(const Grid3& g, int grid_blocks, int requested);
+
+// One problem of a CG phase.
+template <typename T>
+struct CGDesc {
+  Grid3 g;
+  Coef A;
+  Tiling t;
+  long long tile_begin;   // first global tile index of this problem
+  int slot;               // index of this problem's CGState
+  T* x;
+  T* r;
+  T* pa;                  // p buffers: even steps read pa and write pb, odd steps swap
+  T* pb;
+  T* q;
+  double* aux;            // MIXED inner solve: the float64 level solution u += x
+};
+
+// One problem of a residual phase: r = LHS(u) - RHS(f) (= b - A u_I) in float64,
+// written as TR; rr and (optionally) bb reduced; then the CG state is initialised.
+struct ResDesc {
+  Grid3 g;
+  Coef A;
+  Tiling t;
+  long long tile_begin;
+  int slot;             // index of this problem's CGState
+  const double* u;      // level solution, boundary = g
+  View f;               // f at this level's nodes (unused when src is set)
+  const double* src;    // NULL, or b given directly on interior nodes: r = LHS(u) + src
+                        // (the adjoint's A lambda = s with lambda's boundary zero)
+  void* r;              // TR* output
+  double tol_b2;        // tol2 = max(tol_b2 * bb, tol_r2 * rr)
+  double tol_r2;
+  int want_b;           // compute bb (else keep the state's bb)
+  int max_iter;
+  int fixed;            // exact iteration count
+};
+
+// Launch helpers (defined in cg_kernels.cu).  `descs` point to DEVICE copies.
+// One CG step = the stencil launch then the update launch.  When e0/e1/e2 are not
+// null, events are recorded before, between and after the two launches.
+template <typename T>
+cudaError_t launch_cg_step(int nprob, const CGDesc<T>* descs, long long total_tiles, int grid,
+                           CGState* st, double* partials, unsigned* counters,
+                           cudaStream_t s, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr,
+                           cudaEvent_t e2 = nullptr);
+cudaError_t launch_residual(bool out_float, int nprob, const ResDesc* descs,
+                            long long total_tiles, int grid, CGState* st, double* partials,
+                            unsigned* counters, cudaStream_t s);
+cudaError_t launch_add_correction(int nprob, const CGDesc<float>* inner, long long total_tiles,
+                                  int grid, cudaStream_t s);
+int persistent_grid(long long total_tiles);
+
+// Transfer kernels (transfer_kernels.cu).
+struct ProlongDesc {
+  Grid3 g;              // fine grid (h)
+  const double* u2h;    // grid with g.n/2 cells
+  const double* u4h;    // grid with g.n/4 cells
+  View gb;              // Dirichlet data at fine nodes, or p == nullptr
+  double* w;            // fine node array
+  long long block_begin;
+  int nbx, nby, nbz;    // blocks of 32x8x8 fine cells
+};
+cudaError_t launch_exp_finite(int nprob, const ProlongDesc* descs, long long total_blocks,
+                              cudaStream_t s);
+cudaError_t launch_exp_finite_one(const ProlongDesc& desc, cudaStream_t s);
+cudaError_t launch_exp_true(const Grid3& g, const double* uh, const double* u2h, double* ut,
+                            cudaStream_t s);
+cudaError_t launch_boundary_init(const Grid3& g, View gb, double* u, cudaStream_t s);
+cudaError_t launch_adjoint_finish(const Grid3& g, const Coef& A, const double* lam,
+                                  const double* dLdu, double* dLdf, double* dLdg,
+                                  cudaStream_t s);
+
+// Gradient kernels (grad_kernels.cu).
+cudaError_t launch_grad(const Grid3& g, const double* u, double* ux, double* uy, double* uz,
+                        cudaStream_t s);
+
+}  // namespace excmg

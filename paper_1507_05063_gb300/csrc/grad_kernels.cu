@@ -1,0 +1,198 @@
+// Gradient of the FD solution (Section 5, text of Example 1):
+//  * boundary nodes of a line: the one-sided fourth-order five-point formulas
+//      D_0 = (-25/12 u_0 + 4 u_1 - 3 u_2 + 4/3 u_3 - 1/4 u_4) / h, and its mirror at N;
+//  * interior nodes: the compact (Collatz) system
+//      (1/6) D_{i-1} + (4/6) D_i + (1/6) D_{i+1} = (u_{i+1} - u_{i-1}) / (2h),
+//    solved by the Thomas algorithm on every grid line of the direction.
+// The elimination factors of the constant tridiagonal matrix (c'_t = c / m_t,
+// 1 / m_t with m_t = b - a c'_{t-1}) are the same for every line; they converge
+// geometrically (ratio (2 - sqrt 3)^2 ~ 0.072 per step) so a 64-entry table holds them
+// to the last bit and the last entry serves for t >= 64.  The forward sweep's values are
+// kept in the output array and overwritten by the back substitution: no scratch memory.
+// y- and z-lines: one thread per line, neighbouring threads on neighbouring x, so each
+// step is a coalesced row access.  x-lines: one warp per 32 lines, staging 32-node
+// chunks of the lines through shared memory so that global accesses stay coalesced.
+#include <math.h>
+
+#include "excmg_internal.cuh"
+
+namespace excmg {
+
+namespace {
+
+constexpr int kTab = 64;
+
+__device__ void thomas_table(double* cp, double* im, int n) {
+  // a = c = 1/6, b = 4/6
+  const double a = 1.0 / 6.0, c = 1.0 / 6.0, b = 4.0 / 6.0;
+  double prev = 0.0;
+  const int m = n < kTab ? n : kTab;
+  for (int t = 0; t < m; ++t) {
+    const double piv = (t == 0) ? b : b - a * prev;
+    im[t] = 1.0 / piv;
+    cp[t] = c / piv;
+    prev = cp[t];
+  }
+}
+
+__device__ __forceinline__ double d_left(double u0, double u1, double u2, double u3, double u4, double ih) {
+  return (-25.0 / 12.0 * u0 + 4.0 * u1 - 3.0 * u2 + 4.0 / 3.0 * u3 - 0.25 * u4) * ih;
+}
+__device__ __forceinline__ double d_right(double uN, double u1, double u2, double u3, double u4, double ih) {
+  return (25.0 / 12.0 * uN - 4.0 * u1 + 3.0 * u2 - 4.0 / 3.0 * u3 + 0.25 * u4) * ih;
+}
+
+// Lines along a strided direction: node t of line L is base(L) + t * step.  Lines are
+// indexed by (a, b) with a fastest: base = a * sa + b * sb.
+__global__ void __launch_bounds__(kThreads)
+    k_grad_strided(const double* __restrict__ u, double* __restrict__ out, int N, double h,
+                   long long step, int na, int nb, long long sa, long long sb) {
+  __shared__ double cp[kTab], im[kTab];
+  if (threadIdx.x == 0) thomas_table(cp, im, N - 1);
+  __syncthreads();
+  const double ih = 1.0 / h, i2h = 0.5 / h, a6 = 1.0 / 6.0;
+  const long long nl = (long long)na * nb;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < nl;
+       L += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(L % na), b = (int)(L / na);
+    const double* __restrict__ U = u + a * sa + b * sb;
+    double* __restrict__ D = out + a * sa + b * sb;
+    const double D0 = d_left(U[0], U[step], U[2 * step], U[3 * step], U[4 * step], ih);
+    const double DN = d_right(U[N * step], U[(N - 1) * step], U[(N - 2) * step], U[(N - 3) * step],
+                              U[(N - 4) * step], ih);
+    D[0] = D0;
+    D[N * step] = DN;
+    // forward sweep over unknowns t = 0..N-2 (node i = t + 1)
+    double um = U[0], uc = U[step], dp = 0.0;
+    for (int i = 1; i <= N - 1; ++i) {
+      const double up = U[(long long)(i + 1) * step];
+      double rhs = (up - um) * i2h;
+      if (i == 1) rhs -= a6 * D0;
+      if (i == N - 1) rhs -= a6 * DN;
+      const int t = i - 1 < kTab ? i - 1 : kTab - 1;
+      dp = (i == 1) ? rhs * im[0] : (rhs - a6 * dp) * im[t];
+      D[(long long)i * step] = dp;
+      um = uc;
+      uc = up;
+    }
+    // back substitution
+    double x = dp;
+    for (int i = N - 2; i >= 1; --i) {
+      const int t = i - 1 < kTab ? i - 1 : kTab - 1;
+      x = D[(long long)i * step] - cp[t] * x;
+      D[(long long)i * step] = x;
+    }
+  }
+}
+
+// x-lines: one warp handles 32 consecutive lines (line = j + (ny+1) k), chunks of 32
+// x-nodes staged through shared memory.
+__global__ void __launch_bounds__(32)
+    k_grad_x(const double* __restrict__ u, double* __restrict__ out, int N, double h,
+             long long nlines) {
+  __shared__ double cp[kTab], im[kTab];
+  __shared__ double tile[32][35];  // [line][x0-1 .. x0+32]
+  if (threadIdx.x == 0) thomas_table(cp, im, N - 1);
+  __syncwarp();
+  const int lane = threadIdx.x;
+  const long long stride = N + 1;
+  const double ih = 1.0 / h, i2h = 0.5 / h, a6 = 1.0 / 6.0;
+  for (long long L0 = (long long)blockIdx.x * 32; L0 < nlines; L0 += (long long)gridDim.x * 32) {
+    const long long L = L0 + lane;
+    const bool mine = L < nlines;
+    double D0 = 0.0, DN = 0.0;
+    if (mine) {
+      const double* U = u + L * stride;
+      D0 = d_left(U[0], U[1], U[2], U[3], U[4], ih);
+      DN = d_right(U[N], U[N - 1], U[N - 2], U[N - 3], U[N - 4], ih);
+      out[L * stride] = D0;
+      out[L * stride + N] = DN;
+    }
+    // forward sweep, chunk by chunk: unknown nodes i = 1..N-1
+    double dp = 0.0;
+    for (int x0 = 1; x0 <= N - 1; x0 += 32) {
+      const int cnt = min(32, N - x0);  // nodes x0 .. x0+cnt-1
+      __syncwarp();
+      for (int l = 0; l < 32; ++l) {  // coalesced: lane = x offset
+        const long long Ll = L0 + l;
+        if (Ll >= nlines) break;
+        for (int c = lane; c < cnt + 2; c += 32) tile[l][c] = u[Ll * stride + x0 - 1 + c];
+      }
+      __syncwarp();
+      if (mine) {
+        for (int c = 0; c < cnt; ++c) {
+          const int i = x0 + c;
+          double rhs = (tile[lane][c + 2] - tile[lane][c]) * i2h;
+          if (i == 1) rhs -= a6 * D0;
+          if (i == N - 1) rhs -= a6 * DN;
+          const int t = i - 1 < kTab ? i - 1 : kTab - 1;
+          dp = (i == 1) ? rhs * im[0] : (rhs - a6 * dp) * im[t];
+          tile[lane][c] = dp;
+        }
+      }
+      __syncwarp();
+      for (int l = 0; l < 32; ++l) {
+        const long long Ll = L0 + l;
+        if (Ll >= nlines) break;
+        for (int c = lane; c < cnt; c += 32) out[Ll * stride + x0 + c] = tile[l][c];
+      }
+    }
+    // back substitution, chunks from the end
+    double xv = 0.0;
+    bool last = true;
+    for (int x1 = N - 1; x1 >= 1; x1 -= 32) {
+      const int cnt = min(32, x1);  // nodes x1-cnt+1 .. x1
+      const int xs = x1 - cnt + 1;
+      __syncwarp();
+      for (int l = 0; l < 32; ++l) {
+        const long long Ll = L0 + l;
+        if (Ll >= nlines) break;
+        for (int c = lane; c < cnt; c += 32) tile[l][c] = out[Ll * stride + xs + c];
+      }
+      __syncwarp();
+      if (mine) {
+        for (int c = cnt - 1; c >= 0; --c) {
+          const int i = xs + c;
+          if (last) {
+            xv = tile[lane][c];  // x_{N-1} = dp_{N-1}
+            last = false;
+          } else {
+            const int t = i - 1 < kTab ? i - 1 : kTab - 1;
+            xv = tile[lane][c] - cp[t] * xv;
+          }
+          tile[lane][c] = xv;
+        }
+      }
+      last = false;
+      __syncwarp();
+      for (int l = 0; l < 32; ++l) {
+        const long long Ll = L0 + l;
+        if (Ll >= nlines) break;
+        for (int c = lane; c < cnt; c += 32) out[Ll * stride + xs + c] = tile[l][c];
+      }
+    }
+  }
+}
+
+int grid_for(long long items, int per_block) {
+  long long b = (items + per_block - 1) / per_block;
+  if (b > 152 * 32) b = 152 * 32;
+  return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_grad(const Grid3& g, const double* u, double* ux, double* uy, double* uz,
+                        cudaStream_t s) {
+  const long long nlx = (long long)(g.ny + 1) * (g.nz + 1);
+  k_grad_x<<<grid_for(nlx, 32), 32, 0, s>>>(u, ux, g.nx, g.hx, nlx);
+  // y-lines: a = i (fastest), b = k
+  k_grad_strided<<<grid_for((long long)(g.nx + 1) * (g.nz + 1), kThreads), kThreads, 0, s>>>(
+      u, uy, g.ny, g.hy, g.sy, g.nx + 1, g.nz + 1, 1, g.sz);
+  // z-lines: a = i + sy*j flattened (fastest), b unused
+  k_grad_strided<<<grid_for(g.sz, kThreads), kThreads, 0, s>>>(u, uz, g.nz, g.hz, g.sz,
+                                                              (int)g.sz, 1, 1, 0);
+  return cudaGetLastError();
+}
+
+}  // namespace excmg

@@ -213,8 +213,8 @@ def make_inputs(problem: Problem, N, L=None):
     L = problem.L if L is None else L
     x, y, z = node_coords(L, N)
     shape = (N[2] + 1, N[1] + 1, N[0] + 1)
-    u = np.ascontiguousarray(np.broadcast_to(problem.u(x, y, z), shape), dtype=np.float64)
-    f = np.ascontiguousarray(np.broadcast_to(problem.f(x, y, z), shape), dtype=np.float64)
+    u = np.array(np.broadcast_to(problem.u(x, y, z), shape), dtype=np.float64, order="C")
+    f = np.array(np.broadcast_to(problem.f(x, y, z), shape), dtype=np.float64, order="C")
     return f, u.copy(), u
 
 
@@ -222,7 +222,7 @@ def exact_gradient(problem: Problem, N, L=None):
     L = problem.L if L is None else L
     x, y, z = node_coords(L, N)
     shape = (N[2] + 1, N[1] + 1, N[0] + 1)
-    return tuple(np.ascontiguousarray(np.broadcast_to(c, shape), dtype=np.float64)
+    return tuple(np.array(np.broadcast_to(c, shape), dtype=np.float64, order="C")
                  for c in problem.grad(x, y, z))
 
 

@@ -1,0 +1,73 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports every
+symbol include/excmg.h declares, and rejects invalid arguments before any CUDA work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def X():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_05063_gb300 import excmg
+    return excmg
+
+
+def test_exports_every_declared_symbol(X):
+    header = open(os.path.join(ROOT, "include", "excmg.h")).read()
+    declared = set(re.findall(r"\b(excmg_[a-z_]+)\s*\(", header))
+    assert declared, "no declarations found"
+    lib = ctypes.CDLL(X.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(X.EXPORTED)
+
+
+def test_levels_and_workspace_queries(X):
+    g = X.make_grid((1, 1, 1), (32, 32, 32), (4, 4, 4))
+    assert X.excmg_num_levels(ctypes.byref(g)) == 4
+    g2 = X.make_grid((1, 1, 1), (512, 256, 128), (8, 4, 2))
+    assert X.excmg_num_levels(ctypes.byref(g2)) == 7
+    o, _ = X.make_options()
+    assert X.excmg_workspace_size(ctypes.byref(g2), ctypes.byref(o)) > 4 * 8 * 513 * 257 * 129
+    om, _ = X.make_options(precision="mixed")
+    assert 0 < X.excmg_workspace_size(ctypes.byref(g2), ctypes.byref(om)) < \
+        X.excmg_workspace_size(ctypes.byref(g2), ctypes.byref(o))
+
+
+@pytest.mark.parametrize("N,N0", [((32, 32, 32), (3, 3, 3)),      # odd coarsest
+                                  ((32, 32, 30), (4, 4, 4)),      # not a power-of-two refinement
+                                  ((16, 16, 16), (8, 8, 8)),      # only two grids
+                                  ((32, 16, 16), (4, 4, 4))])     # unequal refinement ratios
+def test_invalid_grids_rejected(X, N, N0):
+    g = X.make_grid((1, 1, 1), N, N0)
+    o, _ = X.make_options()
+    assert X.excmg_num_levels(ctypes.byref(g)) == -1
+    assert X.excmg_workspace_size(ctypes.byref(g), ctypes.byref(o)) == 0
+    fake = ctypes.c_void_p(1 << 20)
+    st = X.excmg_solve(ctypes.byref(g), fake, fake, ctypes.byref(o), ctypes.c_void_p(2 << 20),
+                       None, fake, 1 << 30, None, None)
+    assert st == 1
+
+
+def test_invalid_options_rejected(X):
+    g = X.make_grid((1, 1, 1), (32, 32, 32), (4, 4, 4))
+    for kw in ({"precision": 7}, {"eps": -1.0}, {"max_iter": -3}, {"precision": "mixed", "inner_tol": 2.0}):
+        o, _ = X.make_options(**kw)
+        assert X.excmg_workspace_size(ctypes.byref(g), ctypes.byref(o)) == 0
+
+
+def test_small_workspace_rejected(X):
+    g = X.make_grid((1, 1, 1), (32, 32, 32), (4, 4, 4))
+    o, _ = X.make_options()
+    a, b = ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20)
+    ws = ctypes.c_void_p(4 << 20)
+    assert X.excmg_solve(ctypes.byref(g), a, b, ctypes.byref(o), ctypes.c_void_p(3 << 20), None,
+                         ws, 1024, None, None) == 6
+    # misaligned workspace
+    assert X.excmg_solve(ctypes.byref(g), a, b, ctypes.byref(o), ctypes.c_void_p(3 << 20), None,
+                         ctypes.c_void_p((4 << 20) + 8), 1 << 34, None, None) == 6
