@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""EXCMG benchmark: finest-grid unknowns/s of the FP64 EXCMG solve on one GB300.
+
+Workload (default): Poisson on [0,1]^3 with 512 x 256 x 128 cells (hx = 1/512,
+hy = 1/256, hz = 1/128), u = exp(x+y+z), f = 3u, g = u; 7 grids from 8 x 4 x 2; CG
+tolerance 1e-9 on levels >= 2 and 1e-12 on the two coarsest; FP64.  One step = one
+complete excmg_solve (all levels, extrapolation, interpolation, CG) through the C-ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  value = finest-grid interior unknowns solved per second
+summed over ranks (each rank solves its own copy: independent problems, weak scaling,
+no collective on the data path).  e2e = the same metric with the inputs copied from
+pinned host memory and the solution copied back inside the timed region.
+"""
+import os
+
+# the CPU oracle baseline is timed single-threaded
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1507_05063_gb300 import problems as P  # noqa: E402
+
+METRIC = "EXCMG finest-grid unknowns/s at stated L2 error, mixed vs FP64; CG HBM GB/s"
+WORKLOADS = {
+    # name: (problem, L, N, N0, eps, eps_coarse)
+    "c2": ("exp3", (1.0, 1.0, 1.0), (512, 256, 128), (8, 4, 2), 1e-9, 1e-12),
+    "c1": ("sin3", (1.0, 1.0, 1.0), (32, 32, 32), (4, 4, 4), 1e-8, 1e-12),
+    "c3": ("r53", (1.0, 1.0, 1.0), (1024, 512, 512), (8, 4, 4), 1e-9, 1e-12),
+}
+DESCRIPTION = {
+    "c2": "FP64 EXCMG, [0,1]^3, 512x256x128 cells (hx=1/512, hy=1/256, hz=1/128), "
+          "u=exp(x+y+z), f=3u, g=u; 7 grids from 8x4x2; eps 1e-9 (levels>=2), 1e-12 (two coarsest)",
+    "c1": "FP64 EXCMG, [0,1]^3, 32^3 cells, u=sin(pi x)sin(pi y)sin(pi z), f=-3pi^2 u, g=0; "
+          "4 grids from 4^3; eps 1e-8 / 1e-12",
+    "c3": "EXCMG, [0,1]^3, 1024x512x512 cells, u=r^(5/3), f=(40/9) r^(-1/3), g=u; "
+          "8 grids from 8x4x4; eps 1e-9 / 1e-12",
+}
+
+# Algorithmic bytes and float64 operations per node of one launch of each kernel kind
+# (streams the method must move; halo re-reads excluded).  DP ops count FMA, MUL and
+# ADD as one each: they take one issue slot of the FP64 pipe.
+ALGO = {
+    "spmv_f64": {"bytes": 32.0, "dp_ops": 16.0},     # r, p_old in; p, q out
+    "update_f64": {"bytes": 48.0, "dp_ops": 3.0},    # x, p, r, q in; x, r out
+    "spmv_f32": {"bytes": 16.0, "dp_ops": 0.0},
+    "update_f32": {"bytes": 24.0, "dp_ops": 0.0},
+    "residual": {"bytes": 24.0, "dp_ops": 40.0},     # u, f in; r out
+    "exp_finite": {"bytes": 8.0 * (1 + 1 / 8 + 1 / 64), "dp_ops": 8.0},
+    "init": {"bytes": 8.0, "dp_ops": 0.0},
+    "correct": {"bytes": 24.0, "dp_ops": 1.0},
+    "exp_true": {"bytes": 8.0 * (2 + 1 / 8), "dp_ops": 4.0},
+}
+KERNEL_SYMBOL = {"spmv_f64": "k_dir_spmv_dot<double>", "update_f64": "k_update_dot<double>",
+                 "spmv_f32": "k_dir_spmv_dot<float>", "update_f32": "k_update_dot<float>",
+                 "residual": "k_residual", "exp_finite": "k_exp_finite", "init": "k_boundary_init",
+                 "correct": "k_add_correction", "exp_true": "k_exp_true"}
+KERNEL_SOURCE = {"spmv_f64": "cg_kernels.cu", "update_f64": "cg_kernels.cu",
+                 "spmv_f32": "cg_kernels.cu", "update_f32": "cg_kernels.cu",
+                 "residual": "cg_kernels.cu", "exp_finite": "transfer_kernels.cu",
+                 "init": "transfer_kernels.cu", "correct": "cg_kernels.cu",
+                 "exp_true": "transfer_kernels.cu"}
+# FP64 issue rate: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz (maximum SM clock).
+DP_PEAK_GOPS = 2 * 152 * 2.070
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash(fname):
+    with open(os.path.join(ROOT, "paper_1507_05063_gb300", "csrc", fname), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kind):
+    """Per-node DRAM bytes of a kernel from a committed ncu summary, if the kernel source
+    is unchanged since (profiles/ncu_traffic.txt: kind bytes_per_node source_sha)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kind:
+            if parts[2] == source_hash(KERNEL_SOURCE[kind]):
+                return float(parts[1])
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def interior_unknowns(N):
+    return (N[0] - 1) * (N[1] - 1) * (N[2] - 1)
+
+
+def oracle_solve_seconds(wl, f, g):
+    """One complete oracle EXCMG solve of the workload; returns (seconds, u)."""
+    import oracle as O
+    name, L, N, N0, eps, epsc = WORKLOADS[wl]
+    t0 = time.perf_counter()
+    res = O.excmg(f, g, L, N, N0, eps=eps, eps_coarse=epsc, want_utilde=False)
+    return time.perf_counter() - t0, res
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    name, L, N, N0, eps, epsc = WORKLOADS[args.workload]
+    f, g, _ = P.make_inputs(P.PROBLEMS[name], N)
+    for _ in range(args.warmup):
+        oracle_solve_seconds(args.workload, f, g)
+    t = 0.0
+    for _ in range(args.steps):
+        dt, _ = oracle_solve_seconds(args.workload, f, g)
+        t += dt
+    n = interior_unknowns(N)
+    value = n * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (closed-form f, g on the host)",
+            "config": {"workload": DESCRIPTION[args.workload], "unknowns": n},
+            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: one complete oracle EXCMG solve of the workload "
+                                       "(numpy, float64, single thread)"},
+            "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip mixed / CG-rate extras")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_05063_gb300 import excmg as X
+
+    name, L, N, N0, eps, epsc = WORKLOADS[args.workload]
+    f, g, u_exact = P.make_inputs(P.PROBLEMS[name], N)
+    n_unk = interior_unknowns(N)
+    fd = torch.from_numpy(f).to(device)
+    gd = torch.from_numpy(g).to(device)
+    ud = torch.empty_like(fd)
+    opts = dict(eps=eps, eps_coarse=epsc)
+    ws = X.workspace(X.solve_workspace_bytes(L, N, N0, **opts), device)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(max(args.warmup, 0)):
+        X.solve(fd, gd, L, N0, ws=ws, out=ud, **opts)
+
+    # ---- timed region: inputs resident in HBM
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = X.solve(fd, gd, L, N0, ws=ws, out=ud, **opts)
+        launches += res["stats"]["launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms)
+    stats = res["stats"]
+    value = n_unk * world * args.steps / (ms / 1e3)
+
+    # ---- accuracy of the timed solution (host evaluation)
+    uh = ud.cpu().numpy()
+    err_l2 = float(np.sqrt(np.mean((uh - u_exact) ** 2)))
+    err_linf = float(np.max(np.abs(uh - u_exact)))
+
+    # ---- end to end through the C-ABI with host buffers
+    f_pin = torch.from_numpy(f).pin_memory()
+    g_pin = torch.from_numpy(g).pin_memory()
+    u_pin = torch.empty(f.shape, dtype=torch.float64).pin_memory()
+    fd2, gd2, ud2 = torch.empty_like(fd), torch.empty_like(gd), torch.empty_like(fd)
+    barrier()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        fd2.copy_(f_pin, non_blocking=True)
+        gd2.copy_(g_pin, non_blocking=True)
+        X.solve(fd2, gd2, L, N0, ws=ws, out=ud2, **opts)
+        u_pin.copy_(ud2, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3))
+    e2e_value = n_unk * world * args.steps / (ms_e2e / 1e3)
+    assert np.array_equal(u_pin.numpy(), uh), "e2e solution differs from the device-resident one"
+    h2d = f.nbytes + g.nbytes
+    d2h = f.nbytes
+
+    # ---- profiled repeat (events around every launch; not the timed region)
+    prof = X.solve(fd, gd, L, N0, ws=ws, out=ud, profile=1, **opts)["stats"]["profile"]
+    total_prof = sum(v["ms"] for v in prof.values())
+    hbm_peak, peak_kind = load_peaks()
+    kernels = {}
+    for kind, v in prof.items():
+        a = ALGO[kind]
+        t = v["ms"] / 1e3
+        gbs = a["bytes"] * v["nodes"] / t / 1e9 if t > 0 else 0.0
+        gops = a["dp_ops"] * v["nodes"] / t / 1e9 if t > 0 else 0.0
+        t_hbm = a["bytes"] / (hbm_peak * 1e9)
+        t_alu = a["dp_ops"] / (DP_PEAK_GOPS * 1e9)
+        kernels[kind] = {"share": v["ms"] / total_prof if total_prof else 0.0,
+                         "ms": v["ms"], "launches": v["launches"],
+                         "avg_launch_us": 1e3 * v["ms"] / v["launches"],
+                         "GB_s": gbs, "Gdpop_s": gops,
+                         "bound": "alu" if t_alu > t_hbm else "hbm"}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    dk = kernels[dom]
+    launches_dom = prof[dom]["launches"]
+    nodes_per_launch = prof[dom]["nodes"] / launches_dom
+    traffic = recorded_traffic(dom)
+    if dk["bound"] == "alu":
+        roof = {"bound": "alu", "achieved": dk["Gdpop_s"], "peak": DP_PEAK_GOPS,
+                "unit": "G DP-op/s", "frac": dk["Gdpop_s"] / DP_PEAK_GOPS}
+    else:
+        roof = {"bound": "hbm", "achieved": dk["GB_s"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": dk["GB_s"] / hbm_peak}
+    roof.update({"kernel": KERNEL_SYMBOL[dom], "share_of_step": dk["share"],
+                 "traffic": traffic * nodes_per_launch if traffic is not None else None,
+                 "algorithmic_bytes_per_launch": ALGO[dom]["bytes"] * nodes_per_launch,
+                 "avg_launch_us": dk["avg_launch_us"], "peak_source": peak_kind,
+                 "timing": "CUDA events around every launch on the solve's stream, in a "
+                           "profiled repeat of the step after the timed region"})
+
+    line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (closed-form f, g evaluated on the host in float64)",
+            "config": {"workload": DESCRIPTION[args.workload], "unknowns": n_unk,
+                       "levels": stats["levels"], "iters_per_level": stats["iters"],
+                       "relres_finest": stats["relres"][-1],
+                       "error_vs_exact": {"L2_rms": err_l2, "Linf": err_linf},
+                       "parallelism": f"{world} independent replica(s)",
+                       "l2": "inputs larger than L2 (each finest-level array 136 MB > 129 MB L2)"},
+            "gpu_launches": launches, "clocks": clk, "roofline": roof, "kernels": kernels,
+            "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / args.steps}}
+
+    if not args.no_extras:
+        line.update(extras(X, torch, device, L, N, N0, fd, gd, u_exact, opts, err_l2, err_linf,
+                           hbm_peak, args, world))
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, ores = oracle_solve_seconds(args.workload, f, g)
+        uo = ores["u"][-1]
+        line["cpu_baseline"] = {"value": n_unk / secs, "unit": "unknowns/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "one complete oracle EXCMG solve of the same workload "
+                                          "(numpy float64, single thread)",
+                                "seconds": secs, "iters_per_level": ores["iters"],
+                                "gpu_vs_oracle_rel_linf": float(np.max(np.abs(uh - uo)) / np.max(np.abs(uo)))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def extras(X, torch, device, L, N, N0, fd, gd, u_exact, opts, err_l2, err_linf, hbm_peak, args,
+           world):
+    """Mixed-precision EXCMG on the same workload, and the finest-grid CG rates."""
+    out = {}
+    n_unk = interior_unknowns(N)
+    stream = torch.cuda.current_stream()
+    ws_m = X.workspace(X.solve_workspace_bytes(L, N, N0, precision="mixed", **opts), device)
+    um = torch.empty_like(fd)
+    for _ in range(2):
+        X.solve(fd, gd, L, N0, ws=ws_m, out=um, precision="mixed", **opts)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = max(3, args.steps // 2)
+    a.record(stream)
+    for _ in range(k):
+        rm = X.solve(fd, gd, L, N0, ws=ws_m, out=um, precision="mixed", **opts)
+    b.record(stream)
+    torch.cuda.synchronize()
+    msm = a.elapsed_time(b) / k
+    uhm = um.cpu().numpy()
+    e2m = float(np.sqrt(np.mean((uhm - u_exact) ** 2)))
+    eim = float(np.max(np.abs(uhm - u_exact)))
+    out["mixed"] = {"value": n_unk * world / (msm / 1e3), "ms_per_step": msm,
+                    "iters_per_level": rm["stats"]["iters"],
+                    "refinements_per_level": rm["stats"]["refinements"],
+                    "error_vs_exact": {"L2_rms": e2m, "Linf": eim},
+                    "error_ratio_vs_fp64": {"L2": e2m / err_l2, "Linf": eim / err_linf}}
+    # finest-grid CG rates: fixed 20 iterations from the solution, profiled
+    rates = {}
+    for prec in ("fp64", "mixed"):
+        u0 = um.clone()
+        st = X.cg(fd, u0, L, eps=0.0 if prec == "fp64" else 1e-30, fixed_iters=[20] if prec == "fp64" else None,
+                  precision=prec, inner_tol=1e-30, max_iter=20, max_refine=1, profile=1,
+                  allow_not_converged=True)
+        pr = st["profile"]
+        sp = "spmv_f64" if prec == "fp64" else "spmv_f32"
+        up = "update_f64" if prec == "fp64" else "update_f32"
+        if sp not in pr:
+            continue
+        nodes = pr[sp]["nodes"] / pr[sp]["launches"]
+        t_it = (pr[sp]["ms"] + pr[up]["ms"]) / pr[sp]["launches"]
+        byt = (ALGO[sp]["bytes"] + ALGO[up]["bytes"]) * nodes
+        rates[prec] = {"ms_per_iter": t_it, "unknown_iters_per_s": nodes / (t_it / 1e3),
+                       "GB_s": byt / (t_it / 1e3) / 1e9, "frac_hbm": byt / (t_it / 1e3) / 1e9 / hbm_peak,
+                       "spmv_us": 1e3 * pr[sp]["ms"] / pr[sp]["launches"],
+                       "update_us": 1e3 * pr[up]["ms"] / pr[up]["launches"],
+                       "bytes_per_unknown_iter": ALGO[sp]["bytes"] + ALGO[up]["bytes"]}
+        if prec == "fp64":
+            ops = (ALGO[sp]["dp_ops"] + ALGO[up]["dp_ops"]) * nodes
+            rates[prec]["Gdpop_s"] = ops / (t_it / 1e3) / 1e9
+            rates[prec]["frac_alu"] = rates[prec]["Gdpop_s"] / DP_PEAK_GOPS
+    out["cg_finest"] = rates
+    return out
+
+
+if __name__ == "__main__":
+    main()

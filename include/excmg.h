@@ -54,6 +54,20 @@ typedef enum {
 
 #define EXCMG_MAX_LEVELS 24
 
+/* Kernel kinds reported by options.profile. */
+typedef enum {
+  EXCMG_K_SPMV_F64 = 0,   /* p = r + beta p, q = A p, p.q            (float64 CG) */
+  EXCMG_K_UPDATE_F64 = 1, /* x += alpha p, r -= alpha q, r.r        (float64 CG) */
+  EXCMG_K_SPMV_F32 = 2,   /* the same in float32 (MIXED inner solves) */
+  EXCMG_K_UPDATE_F32 = 3,
+  EXCMG_K_RESIDUAL = 4,   /* r = b - A u in float64, ||r||, ||b|| */
+  EXCMG_K_EXP_FINITE = 5, /* w_h = EXP_finite(u_2h, u_4h) */
+  EXCMG_K_INIT = 6,       /* boundary data, zero interior (levels 0, 1) */
+  EXCMG_K_CORRECT = 7,    /* u += e (MIXED) */
+  EXCMG_K_EXP_TRUE = 8,   /* u~_h = EXP_true(u_h, u_2h) */
+  EXCMG_KERNEL_KINDS = 9
+} excmg_kernel_kind;
+
 /* Box and grids (Section 2: hx = Lx/Nx ...; Algorithm 1: coarsest grid H, L levels). */
 typedef struct {
   double Lx, Ly, Lz;  /* box lengths, > 0 */
@@ -75,9 +89,9 @@ typedef struct {
                               many CG iterations on each level (FP64 only; parity tests) */
   int tile_z;              /* z-slab depth of the stencil kernels; 0 = library default */
   int chunk;               /* CG iterations enqueued between convergence reads; 0 = auto */
-  int profile;             /* nonzero: time every finest-level CG launch with CUDA events on
-                              the caller's stream (stats.prof_*); adds one event record per
-                              launch */
+  int profile;             /* nonzero: time every kernel launch of excmg_solve / excmg_cg
+                              with CUDA events on the caller's stream (stats.prof_*);
+                              single-problem calls only; adds two event records per launch */
 } excmg_options;
 
 /* Per-solve statistics, valid when the call returns. */
@@ -89,9 +103,12 @@ typedef struct {
   double relres[EXCMG_MAX_LEVELS];   /* final ||r||/||b|| per level (recursive residual
                                         for FP64; true float64 residual for MIXED) */
   long long launches;                /* kernels this call launched (all levels) */
-  int prof_steps;                    /* profile: CG steps timed on the finest level */
-  double prof_spmv_ms;               /* profile: summed time of their stencil launches */
-  double prof_update_ms;             /* profile: summed time of their update launches */
+  /* options.profile: per kernel kind (excmg_kernel_kind), summed CUDA-event time of its
+     launches that did work, their count, and the node count they covered in total
+     (CG launches issued after convergence return at once and are not counted) */
+  double prof_ms[EXCMG_KERNEL_KINDS];
+  long long prof_launches[EXCMG_KERNEL_KINDS];
+  double prof_nodes[EXCMG_KERNEL_KINDS];
 } excmg_stats;
 
 /* Writes the defaults: FP64, eps 1e-9, eps_coarse 1e-12, max_iter 100000,

@@ -225,21 +225,36 @@ struct Prob {
   }
 };
 
-// Event timing of the finest-level CG launches (options.profile).
+// Event timing of kernel launches (options.profile): one record per launch.
 struct Prof {
+  struct Rec {
+    int kind;
+    size_t e0, e1;   // indices into pool
+    double nodes;
+    bool real;
+  };
   std::vector<cudaEvent_t> pool;
-  int steps = 0;
-  double spmv_ms = 0.0, update_ms = 0.0;
+  std::vector<Rec> recs;
   ~Prof() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
   }
-  cudaEvent_t get(size_t i) {
-    while (pool.size() <= i) {
-      cudaEvent_t e;
-      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-      pool.push_back(e);
+  size_t event() {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) e = nullptr;
+    pool.push_back(e);
+    return pool.size() - 1;
+  }
+  // Sum the records into stats after the stream has been synchronised.
+  void report(excmg_stats* st) const {
+    if (!st) return;
+    for (const Rec& r : recs) {
+      if (!r.real || !pool[r.e0] || !pool[r.e1]) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pool[r.e0], pool[r.e1]) != cudaSuccess) continue;
+      st->prof_ms[r.kind] += ms;
+      st->prof_launches[r.kind] += 1;
+      st->prof_nodes[r.kind] += r.nodes;
     }
-    return pool[i];
   }
 };
 
@@ -248,7 +263,19 @@ struct Ctx {
   Header H;
   cudaStream_t s;
   long long* launches = nullptr;  // kernels launched by this call
-  Prof* prof = nullptr;           // set while the finest level of a profiled call runs
+  Prof* prof = nullptr;           // set when the call is profiled
+  // Bracket one launch: record an event before `fn` and after it.
+  template <typename F>
+  cudaError_t timed(int kind, double nodes, F fn) const {
+    if (launches) *launches += 1;
+    if (!prof) return fn();
+    const size_t a = prof->event(), b = prof->event();
+    if (prof->pool[a]) cudaEventRecord(prof->pool[a], s);
+    cudaError_t e = fn();
+    if (prof->pool[b]) cudaEventRecord(prof->pool[b], s);
+    prof->recs.push_back({kind, a, b, nodes, true});
+    return e;
+  }
   CGState* st() const { return reinterpret_cast<CGState*>(ws + H.st); }
   unsigned* counters() const { return reinterpret_cast<unsigned*>(ws + H.counters); }
   double* partials() const { return reinterpret_cast<double*>(ws + H.partials); }
@@ -270,17 +297,21 @@ excmg_status read_states(const Ctx& c, int nprob, std::vector<CGState>& hs) {
 template <typename T>
 excmg_status cg_loop(const Ctx& c, int n, const CGDesc<T>* ddesc, long long tiles, int grid,
                      const std::vector<int>& slots, int nslots, int chunk0,
-                     std::vector<CGState>& hs) {
+                     std::vector<CGState>& hs, double nodes) {
   int chunk = chunk0 > 0 ? chunk0 : 4;
   Prof* prof = (c.prof && n == 1) ? c.prof : nullptr;
+  const int kspmv = sizeof(T) == 8 ? EXCMG_K_SPMV_F64 : EXCMG_K_SPMV_F32;
+  const int kupd = sizeof(T) == 8 ? EXCMG_K_UPDATE_F64 : EXCMG_K_UPDATE_F32;
+  const size_t rec0 = prof ? prof->recs.size() : 0;
   int launched = 0;
   for (;;) {
     for (int m = 0; m < chunk; ++m) {
       if (prof) {
-        const size_t b = 3 * (size_t)launched;
-        cudaEvent_t e0 = prof->get(b), e1 = prof->get(b + 1), e2 = prof->get(b + 2);
-        CK(launch_cg_step<T>(n, ddesc, tiles, grid, c.st(), c.partials(), c.counters(), c.s, e0,
-                             e1, e2));
+        const size_t e0 = prof->event(), e1 = prof->event(), e2 = prof->event();
+        CK(launch_cg_step<T>(n, ddesc, tiles, grid, c.st(), c.partials(), c.counters(), c.s,
+                             prof->pool[e0], prof->pool[e1], prof->pool[e2]));
+        prof->recs.push_back({kspmv, e0, e1, nodes, true});
+        prof->recs.push_back({kupd, e1, e2, nodes, true});
       } else {
         CK(launch_cg_step<T>(n, ddesc, tiles, grid, c.st(), c.partials(), c.counters(), c.s));
       }
@@ -295,16 +326,9 @@ excmg_status cg_loop(const Ctx& c, int n, const CGDesc<T>* ddesc, long long tile
     if (chunk0 <= 0) chunk = std::min(chunk * 2, 64);
   }
   if (prof) {
-    // steps after convergence returned at once; time only the steps that ran
+    // steps issued after convergence returned at once: not counted
     const int real = std::min(hs[slots[0]].iter, launched);
-    for (int k = 0; k < real; ++k) {
-      float a = 0.f, b = 0.f;
-      CK(cudaEventElapsedTime(&a, prof->pool[3 * k], prof->pool[3 * k + 1]));
-      CK(cudaEventElapsedTime(&b, prof->pool[3 * k + 1], prof->pool[3 * k + 2]));
-      prof->spmv_ms += a;
-      prof->update_ms += b;
-    }
-    prof->steps += real;
+    for (size_t k = rec0 + 2 * (size_t)real; k < prof->recs.size(); ++k) prof->recs[k].real = false;
   }
   return EXCMG_OK;
 }
@@ -377,6 +401,8 @@ excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_opt
     hr.push_back(r);
   }
   if (n == 0) return EXCMG_OK;
+  double nodes_sum = 0.0;
+  for (auto& it : items) nodes_sum += (double)it.nodes;
   if (!mixed) {
     std::vector<CGDesc<double>> hd;
     std::vector<int> slots;
@@ -387,9 +413,10 @@ excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_opt
     const int grid = tiles_grid(tiles);
     CK(cudaMemcpyAsync(c.resd(), hr.data(), sizeof(ResDesc) * n, cudaMemcpyHostToDevice, c.s));
     CK(cudaMemcpyAsync(c.cgd(), hd.data(), sizeof(CGDesc<double>) * n, cudaMemcpyHostToDevice, c.s));
-    CK(launch_residual(false, n, c.resd(), tiles, grid, c.st(), c.partials(), c.counters(), c.s));
-    if (c.launches) *c.launches += 1;
-    excmg_status e = cg_loop<double>(c, n, c.cgd(), tiles, grid, slots, nslots, o->chunk, hs);
+    CK(c.timed(EXCMG_K_RESIDUAL, nodes_sum, [&] {
+      return launch_residual(false, n, c.resd(), tiles, grid, c.st(), c.partials(), c.counters(), c.s);
+    }));
+    excmg_status e = cg_loop<double>(c, n, c.cgd(), tiles, grid, slots, nslots, o->chunk, hs, nodes_sum);
     if (e != EXCMG_OK) return e;
     for (auto& it : items) {
       const CGState& S = hs[it.d64.slot];
@@ -413,9 +440,12 @@ excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_opt
       rr.push_back(r);
     }
     const int nr = (int)rr.size();
+    double rnodes = 0.0;
+    for (int a : cur) rnodes += (double)items[a].nodes;
     CK(cudaMemcpyAsync(c.resd(), rr.data(), sizeof(ResDesc) * nr, cudaMemcpyHostToDevice, c.s));
-    CK(launch_residual(true, nr, c.resd(), rt, tiles_grid(rt), c.st(), c.partials(), c.counters(), c.s));
-    if (c.launches) *c.launches += 1;
+    CK(c.timed(EXCMG_K_RESIDUAL, rnodes, [&] {
+      return launch_residual(true, nr, c.resd(), rt, tiles_grid(rt), c.st(), c.partials(), c.counters(), c.s);
+    }));
     excmg_status e = read_states(c, nslots, hs);
     if (e != EXCMG_OK) return e;
     std::vector<int> next;
@@ -445,16 +475,17 @@ excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_opt
     }
     const int nf = (int)fd.size();
     const int fgrid = tiles_grid(ft);
+    double fnodes = 0.0;
+    for (int a : next) fnodes += (double)items[a].nodes;
     CK(cudaMemcpyAsync(c.cgf(), fd.data(), sizeof(CGDesc<float>) * nf, cudaMemcpyHostToDevice, c.s));
-    e = cg_loop<float>(c, nf, c.cgf(), ft, fgrid, fslots, nslots, o->chunk, hs);
+    e = cg_loop<float>(c, nf, c.cgf(), ft, fgrid, fslots, nslots, o->chunk, hs, fnodes);
     if (e != EXCMG_OK) return e;
     for (int a : next) {
       items[a].iters += hs[items[a].d32.slot].iter;
       items[a].refs += 1;
       // an inner solve that hits max_iter is not fatal: refinement continues
     }
-    CK(launch_add_correction(nf, c.cgf(), ft, fgrid, c.s));
-    if (c.launches) *c.launches += 1;
+    CK(c.timed(EXCMG_K_CORRECT, fnodes, [&] { return launch_add_correction(nf, c.cgf(), ft, fgrid, c.s); }));
     cur = next;
   }
 }
@@ -502,6 +533,8 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
   long long launches = 0;
   Ctx c = c0;
   c.launches = &launches;
+  Prof prof;
+  if (o->profile && np == 1) c.prof = &prof;
   struct Report {
     excmg_stats* st;
     long long* n;
@@ -538,13 +571,13 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
     // 1. initial guess: zero inside (levels 0, 1) or w_h = EXP_finite(u_2h, u_4h)
     int npro = 0;
     long long pblocks = 0;
+    double pnodes = 0.0;
     for (int a = 0; a < na; ++a) {
       Prob& p = P[act[a]];
       const int l = lev[a];
       const Grid3 g = p.grid(l);
       if (l < 2) {
-        CK(launch_boundary_init(g, p.gview(l), p.level_u(l), c.s));
-        if (c.launches) *c.launches += 1;
+        CK(c.timed(EXCMG_K_INIT, (double)g.nodes(), [&] { return launch_boundary_init(g, p.gview(l), p.level_u(l), c.s); }));
       } else {
         ProlongDesc d;
         d.g = g;
@@ -557,13 +590,13 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
         d.nbz = g.nz / 8;
         d.block_begin = pblocks;
         pblocks += (long long)d.nbx * d.nby * d.nbz;
+        pnodes += (double)g.nodes();
         hp[npro++] = d;
       }
     }
     if (npro > 0) {
       CK(cudaMemcpyAsync(c.prold(), hp.data(), sizeof(ProlongDesc) * npro, cudaMemcpyHostToDevice, c.s));
-      CK(launch_exp_finite(npro, c.prold(), pblocks, c.s));
-      if (c.launches) *c.launches += 1;
+      CK(c.timed(EXCMG_K_EXP_FINITE, pnodes, [&] { return launch_exp_finite(npro, c.prold(), pblocks, c.s); }));
     }
     // 2. CG (FP64) or refinement (MIXED) on every active problem's level
     std::vector<Item> items;
@@ -572,16 +605,8 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
       items.push_back(make_item(P[act[a]], lev[a], act[a], o));
       if (o->fixed_iters) fixed.push_back(o->fixed_iters[lev[a]]);
     }
-    Ctx cc = c;
-    Prof prof;
-    if (o->profile && np == 1 && phase == maxL - 1) cc.prof = &prof;
-    excmg_status e = solve_items(cc, items, o, np, o->fixed_iters ? fixed.data() : nullptr);
+    excmg_status e = solve_items(c, items, o, np, o->fixed_iters ? fixed.data() : nullptr);
     if (e != EXCMG_OK) return e;
-    if (cc.prof && stats) {
-      stats[0].prof_steps = prof.steps;
-      stats[0].prof_spmv_ms = prof.spmv_ms;
-      stats[0].prof_update_ms = prof.update_ms;
-    }
     for (int a = 0; a < na; ++a) {
       const Item& it = items[a];
       if (stats) {
@@ -596,11 +621,13 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
   if (u_tilde && np == 1) {
     Prob& p = P[0];
     const int l = (int)p.lv.size() - 1;
-    CK(launch_exp_true(p.grid(l), p.level_u(l), p.level_u(l - 1), u_tilde, c.s));
-    if (c.launches) *c.launches += 1;
+    CK(c.timed(EXCMG_K_EXP_TRUE, (double)p.grid(l).nodes(), [&] {
+      return launch_exp_true(p.grid(l), p.level_u(l), p.level_u(l - 1), u_tilde, c.s);
+    }));
   }
   CK(cudaStreamSynchronize(c.s));
   CK(cudaGetLastError());
+  if (c.prof) prof.report(stats);
   return result;
 }
 
@@ -797,12 +824,18 @@ excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_optio
   const int l = (int)lv.size() - 1;
   std::vector<Item> items{make_item(p, l, 0, opt)};
   items[0].eps = opt->eps;
+  long long launches = 0;
+  Prof prof;
+  c.launches = &launches;
+  if (opt->profile) c.prof = &prof;
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
   excmg_status e = solve_items(c, items, opt, 1, opt->fixed_iters);
   if (e != EXCMG_OK) return e;
   CK(cudaStreamSynchronize(c.s));
   if (stats) {
     memset(stats, 0, sizeof(*stats));
+    stats->launches = launches;
+    prof.report(stats);
     stats->levels = 1;
     stats->N[0][0] = lv[l].nx;
     stats->N[0][1] = lv[l].ny;

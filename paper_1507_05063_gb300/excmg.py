@@ -25,6 +25,9 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 MAX_LEVELS = 24
 FP64, MIXED = 0, 1
+KERNEL_NAMES = ["spmv_f64", "update_f64", "spmv_f32", "update_f32", "residual", "exp_finite",
+                "init", "correct", "exp_true"]
+KERNEL_KINDS = len(KERNEL_NAMES)
 STATUS = {0: "EXCMG_OK", 1: "EXCMG_ERR_INVALID_ARG", 2: "EXCMG_ERR_NOT_CONVERGED",
           3: "EXCMG_ERR_CUDA", 4: "EXCMG_ERR_NONFINITE", 5: "EXCMG_ERR_TIMEOUT",
           6: "EXCMG_ERR_WORKSPACE"}
@@ -49,16 +52,19 @@ class Stats(ctypes.Structure):
                 ("iters", ctypes.c_int * MAX_LEVELS),
                 ("refinements", ctypes.c_int * MAX_LEVELS),
                 ("relres", ctypes.c_double * MAX_LEVELS), ("launches", ctypes.c_longlong),
-                ("prof_steps", ctypes.c_int), ("prof_spmv_ms", ctypes.c_double),
-                ("prof_update_ms", ctypes.c_double)]
+                ("prof_ms", ctypes.c_double * KERNEL_KINDS),
+                ("prof_launches", ctypes.c_longlong * KERNEL_KINDS),
+                ("prof_nodes", ctypes.c_double * KERNEL_KINDS)]
 
     def to_dict(self):
         n = self.levels
         return {"levels": n, "N": [tuple(self.N[l]) for l in range(n)],
                 "iters": list(self.iters[:n]), "refinements": list(self.refinements[:n]),
                 "relres": list(self.relres[:n]), "launches": int(self.launches),
-                "prof_steps": int(self.prof_steps), "prof_spmv_ms": float(self.prof_spmv_ms),
-                "prof_update_ms": float(self.prof_update_ms)}
+                "profile": {KERNEL_NAMES[k]: {"ms": float(self.prof_ms[k]),
+                                              "launches": int(self.prof_launches[k]),
+                                              "nodes": float(self.prof_nodes[k])}
+                            for k in range(KERNEL_KINDS) if self.prof_launches[k] > 0}}
 
 
 _P = ctypes.c_void_p
