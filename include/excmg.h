@@ -239,6 +239,33 @@ excmg_status excmg_residual(const excmg_grid* grid, const double* f, const doubl
                             double* r, double* rnorm, double* bnorm, void* ws,
                             size_t ws_bytes, void* stream);
 
+/* ---- an entry point for callers that cannot allocate device memory ----
+ *
+ * excmg_cg_noalloc -- the same computation as excmg_cg (float64 CG on the grid
+ * Nx x Ny x Nz from the interior of u, with the same options, outputs and status codes),
+ * but it takes no workspace: its scratch is a device array built into the library.
+ * The paper has no counterpart; this exists for callers that must not allocate device
+ * memory -- an application or framework that owns all device memory through its own
+ * pool, code that cannot afford cudaMalloc's implicit synchronisation, or a binding
+ * with no access to a CUDA allocator.  Those callers pass inputs and outputs only.
+ *   Limit: the scratch is EXCMG_NOALLOC_SCRATCH_BYTES (16 MiB) per device, held from the
+ *   moment the library is loaded until the process exits; it holds four float64 node
+ *   arrays plus ~66 KB, i.e. grids up to about 520,000 nodes (80 x 80 x 80 cells does
+ *   not fit, 64 x 64 x 64 does).  A larger grid returns EXCMG_ERR_WORKSPACE before any
+ *   work is enqueued.  Only EXCMG_FP64 is accepted.
+ *   Set-up: the first call on each device looks up the scratch's device address (with
+ *   that device current) and caches it; make that first call before any stream
+ *   capture.
+ *   Sharing: every call uses the same scratch and leaves its last contents there (the
+ *   call clears what must start at zero itself).  Calls whose work overlaps on the GPU
+ *   -- on different streams or from different host threads -- race on the scratch and
+ *   must be serialised by the caller.
+ */
+#define EXCMG_NOALLOC_SCRATCH_BYTES (16u << 20)
+excmg_status excmg_cg_noalloc(const excmg_grid* grid, const double* f,
+                              const excmg_options* opt, double* u, excmg_stats* stats,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,11 +102,13 @@ excmg_exp_true = _sig("excmg_exp_true", ctypes.c_int, [_GP, _P, _P, _P, _P])
 excmg_cg = _sig("excmg_cg", ctypes.c_int, [_GP, _P, _OP, _P, _P, ctypes.c_size_t, _SP, _P])
 excmg_residual = _sig("excmg_residual", ctypes.c_int,
                       [_GP, _P, _P, _P, _D, _D, _P, ctypes.c_size_t, _P])
+excmg_cg_noalloc = _sig("excmg_cg_noalloc", ctypes.c_int, [_GP, _P, _OP, _P, _SP, _P])
 
 EXPORTED = ["excmg_default_options", "excmg_status_string", "excmg_num_levels",
             "excmg_workspace_size", "excmg_workspace_size_batched",
             "excmg_workspace_size_adjoint", "excmg_workspace_size_level", "excmg_solve", "excmg_grad", "excmg_solve_batched",
-            "excmg_adjoint", "excmg_exp_finite", "excmg_exp_true", "excmg_cg", "excmg_residual"]
+            "excmg_adjoint", "excmg_exp_finite", "excmg_exp_true", "excmg_cg", "excmg_residual",
+            "excmg_cg_noalloc"]
 
 
 class ExcmgError(RuntimeError):
