@@ -63,16 +63,21 @@ ALGO = {
     "init": {"bytes": 8.0, "dp_ops": 0.0},
     "correct": {"bytes": 24.0, "dp_ops": 1.0},
     "exp_true": {"bytes": 8.0 * (2 + 1 / 8), "dp_ops": 4.0},
+    # persistent CG: per node and CG step (the two fused bodies above)
+    "cg_f64": {"bytes": 80.0, "dp_ops": 19.0},
+    "cg_f32": {"bytes": 40.0, "dp_ops": 0.0},
 }
 KERNEL_SYMBOL = {"spmv_f64": "k_dir_spmv_dot<double>", "update_f64": "k_update_dot<double>",
                  "spmv_f32": "k_dir_spmv_dot<float>", "update_f32": "k_update_dot<float>",
                  "residual": "k_residual", "exp_finite": "k_exp_finite", "init": "k_boundary_init",
-                 "correct": "k_add_correction", "exp_true": "k_exp_true"}
+                 "correct": "k_add_correction", "exp_true": "k_exp_true",
+                 "cg_f64": "k_cg_persistent<double>", "cg_f32": "k_cg_persistent<float>"}
 KERNEL_SOURCE = {"spmv_f64": "cg_kernels.cu", "update_f64": "cg_kernels.cu",
                  "spmv_f32": "cg_kernels.cu", "update_f32": "cg_kernels.cu",
                  "residual": "cg_kernels.cu", "exp_finite": "transfer_kernels.cu",
                  "init": "transfer_kernels.cu", "correct": "cg_kernels.cu",
-                 "exp_true": "transfer_kernels.cu"}
+                 "exp_true": "transfer_kernels.cu", "cg_f64": "cg_kernels.cu",
+                 "cg_f32": "cg_kernels.cu"}
 # FP64 issue rate: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz (maximum SM clock).
 DP_PEAK_GOPS = 2 * 152 * 2.070
 
@@ -321,7 +326,7 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     dk = kernels[dom]
     launches_dom = prof[dom]["launches"]
-    nodes_per_launch = prof[dom]["nodes"] / launches_dom
+    nodes_per_launch = prof[dom]["nodes"] / launches_dom  # node-steps for persistent CG
     traffic = recorded_traffic(dom)
     if dk["bound"] == "alu":
         roof = {"bound": "alu", "achieved": dk["Gdpop_s"], "peak": DP_PEAK_GOPS,
@@ -404,20 +409,20 @@ def extras(X, torch, device, L, N, N0, fd, gd, u_exact, opts, err_l2, err_linf, 
                   precision=prec, inner_tol=1e-30, max_iter=20, max_refine=1, profile=1,
                   allow_not_converged=True)
         pr = st["profile"]
-        sp = "spmv_f64" if prec == "fp64" else "spmv_f32"
-        up = "update_f64" if prec == "fp64" else "update_f32"
-        if sp not in pr:
+        kind = "cg_f64" if prec == "fp64" else "cg_f32"
+        if kind not in pr:
             continue
-        nodes = pr[sp]["nodes"] / pr[sp]["launches"]
-        t_it = (pr[sp]["ms"] + pr[up]["ms"]) / pr[sp]["launches"]
-        byt = (ALGO[sp]["bytes"] + ALGO[up]["bytes"]) * nodes
-        rates[prec] = {"ms_per_iter": t_it, "unknown_iters_per_s": nodes / (t_it / 1e3),
+        steps = st["iters"][0]
+        node_steps = pr[kind]["nodes"]
+        t_it = pr[kind]["ms"] / max(steps, 1)
+        nodes = node_steps / max(steps, 1)
+        byt = ALGO[kind]["bytes"] * nodes
+        rates[prec] = {"kernel": KERNEL_SYMBOL[kind], "steps": steps, "ms_per_iter": t_it,
+                       "unknown_iters_per_s": nodes / (t_it / 1e3),
                        "GB_s": byt / (t_it / 1e3) / 1e9, "frac_hbm": byt / (t_it / 1e3) / 1e9 / hbm_peak,
-                       "spmv_us": 1e3 * pr[sp]["ms"] / pr[sp]["launches"],
-                       "update_us": 1e3 * pr[up]["ms"] / pr[up]["launches"],
-                       "bytes_per_unknown_iter": ALGO[sp]["bytes"] + ALGO[up]["bytes"]}
+                       "bytes_per_unknown_iter": ALGO[kind]["bytes"]}
         if prec == "fp64":
-            ops = (ALGO[sp]["dp_ops"] + ALGO[up]["dp_ops"]) * nodes
+            ops = ALGO[kind]["dp_ops"] * nodes
             rates[prec]["Gdpop_s"] = ops / (t_it / 1e3) / 1e9
             rates[prec]["frac_alu"] = rates[prec]["Gdpop_s"] / DP_PEAK_GOPS
     out["cg_finest"] = rates

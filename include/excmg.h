@@ -65,7 +65,10 @@ typedef enum {
   EXCMG_K_INIT = 6,       /* boundary data, zero interior (levels 0, 1) */
   EXCMG_K_CORRECT = 7,    /* u += e (MIXED) */
   EXCMG_K_EXP_TRUE = 8,   /* u~_h = EXP_true(u_h, u_2h) */
-  EXCMG_KERNEL_KINDS = 9
+  EXCMG_K_CG_F64 = 9,     /* all CG steps of a level in one persistent launch (float64);
+                             prof_nodes counts nodes x steps */
+  EXCMG_K_CG_F32 = 10,    /* the same for a float32 inner solve */
+  EXCMG_KERNEL_KINDS = 11
 } excmg_kernel_kind;
 
 /* Box and grids (Section 2: hx = Lx/Nx ...; Algorithm 1: coarsest grid H, L levels). */

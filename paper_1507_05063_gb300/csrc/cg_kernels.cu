@@ -18,6 +18,8 @@
 // block, and a fixed-order sum of the per-block partials by the last block to arrive.
 #include <math.h>
 
+#include <algorithm>
+
 #include "excmg_internal.cuh"
 
 namespace excmg {
@@ -183,6 +185,133 @@ struct FinRes {
   }
 };
 
+// Loads of CG vectors bypass L1 (ld.global.cg): in the persistent kernel other blocks
+// rewrite them between grid barriers, and L1 is not coherent across SMs.
+__device__ __forceinline__ double ldv(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldv(const float* p) { return __ldcg(p); }
+
+// One stencil tile: p_new = r + beta p_old (p = r when first), q = A p_new on the tile's
+// nodes, returns this thread's share of p.q.  `sp` is the block's staging buffer and
+// `buf` its current half (advanced per plane).  All threads of the block must call.
+// The (kTX+2) x (kTY+2) halo plane is staged by the block's threads, at most two
+// elements each; the loads of plane k+1 are issued into registers before the barrier
+// and arithmetic of plane k, so global-memory latency overlaps the stencil work.
+constexpr int kStage = (kTX + 2) * (kTY + 2);
+static_assert(kStage <= 2 * kThreads, "a staged plane must need at most two loads per thread");
+
+template <typename T>
+struct PlaneLoad {
+  T r0, p0, r1, p1;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_plane(PlaneLoad<T>& L, const Grid3& g, const TileXYZ& c, int kk,
+                                           bool first, const T* __restrict__ r,
+                                           const T* __restrict__ pold) {
+  L.r0 = L.p0 = L.r1 = L.p1 = T(0);
+  if (kk < 0 || kk > g.nz) return;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int idx = threadIdx.x + h * kThreads;
+    if (idx >= kStage) break;
+    const int ly = idx / (kTX + 2), lx = idx - ly * (kTX + 2);
+    const int gi = c.x0 - 1 + lx, gj = c.y0 - 1 + ly;
+    if (gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny) {
+      const long long o = gi + gj * g.sy + (long long)kk * g.sz;
+      const T rv = ldv(r + o);
+      const T pv = first ? T(0) : ldv(pold + o);
+      if (h == 0) {
+        L.r0 = rv;
+        L.p0 = pv;
+      } else {
+        L.r1 = rv;
+        L.p1 = pv;
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_plane(const PlaneLoad<T>& L, T beta,
+                                            T (*plane)[kTX + 2]) {
+  T* flat = &plane[0][0];
+  flat[threadIdx.x] = fmaT(beta, L.p0, L.r0);
+  if (threadIdx.x + kThreads < kStage) flat[threadIdx.x + kThreads] = fmaT(beta, L.p1, L.r1);
+}
+
+template <typename T>
+__device__ __forceinline__ T spmv_tile(const CGDesc<T>& d, long long lt, bool first, T beta,
+                                       const T* __restrict__ pold, T* __restrict__ pnew,
+                                       T (*sp)[kTY + 2][kTX + 2], int& buf) {
+  const Grid3 g = d.g;
+  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+  const T* __restrict__ r = d.r;
+  T* __restrict__ q = d.q;
+  const TileXYZ c = tile_coords(g, d.t, lt);
+  const int i = c.x0 + tx, j = c.y0 + ty;
+  const bool own = (i <= g.nx) && (j <= g.ny);
+  const bool inxy = (i > 0) && (i < g.nx) && (j > 0) && (j < g.ny);
+  const T c0 = (T)d.A.c0, fx = (T)d.A.fx, fy = (T)d.A.fy, fz = (T)d.A.fz;
+  const T exy = (T)d.A.exy, exz = (T)d.A.exz, eyz = (T)d.A.eyz;
+  const T bta = first ? T(0) : beta;
+  T Pm1 = T(0), Cm1 = T(0), Tm1 = T(0), Tm2 = T(0), tacc = T(0);
+  PlaneLoad<T> nxt;
+  load_plane(nxt, g, c, c.z0 - 1, first, r, pold);
+  for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
+    store_plane(nxt, bta, sp[buf]);
+    if (kk < c.z1) load_plane(nxt, g, c, kk + 1, first, r, pold);
+    __syncthreads();
+    const T P = sp[buf][ty + 1][tx + 1];
+    const T SX = sp[buf][ty + 1][tx] + sp[buf][ty + 1][tx + 2];
+    const T SY = sp[buf][ty][tx + 1] + sp[buf][ty + 2][tx + 1];
+    const T EXY = (sp[buf][ty][tx] + sp[buf][ty][tx + 2]) + (sp[buf][ty + 2][tx] + sp[buf][ty + 2][tx + 2]);
+    const T Ck = fmaT(c0, P, fmaT(fx, SX, fmaT(fy, SY, exy * EXY)));
+    const T Tk = fmaT(fz, P, fmaT(exz, SX, eyz * SY));
+    const int kc = kk - 1;
+    if (kc >= c.z0 && own) {
+      const long long o = i + j * g.sy + (long long)kc * g.sz;
+      const bool interior = inxy && kc > 0 && kc < g.nz;
+      const T qv = interior ? (Cm1 + Tm2) + Tk : T(0);
+      pnew[o] = Pm1;
+      q[o] = qv;
+      tacc = fmaT(Pm1, qv, tacc);
+    }
+    Tm2 = Tm1;
+    Tm1 = Tk;
+    Cm1 = Ck;
+    Pm1 = P;
+    buf ^= 1;
+  }
+  return tacc;
+}
+
+// One update tile: x += alpha p, r -= alpha q on the tile's nodes; returns this thread's
+// share of r.r.
+template <typename T>
+__device__ __forceinline__ T update_tile(const CGDesc<T>& d, long long lt, T alpha,
+                                         const T* __restrict__ pn) {
+  const Grid3 g = d.g;
+  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+  const T* __restrict__ q = d.q;
+  T* __restrict__ x = d.x;
+  T* __restrict__ r = d.r;
+  const TileXYZ c = tile_coords(g, d.t, lt);
+  const int i = c.x0 + tx, j = c.y0 + ty;
+  T tacc = T(0);
+  if (i <= g.nx && j <= g.ny) {
+    long long o = i + j * g.sy + (long long)c.z0 * g.sz;
+#pragma unroll 4
+    for (int k = c.z0; k < c.z1; ++k, o += g.sz) {
+      const T xv = fmaT(alpha, ldv(pn + o), ldv(x + o));
+      const T rv = fmaT(-alpha, ldv(q + o), ldv(r + o));
+      x[o] = xv;
+      r[o] = rv;
+      tacc = fmaT(rv, rv, tacc);
+    }
+  }
+  return tacc;
+}
+
 // ---------------------------------------------------------------------------------
 // K1: p_new = r + beta p_old, q = A p_new, sum p.q
 // ---------------------------------------------------------------------------------
@@ -198,7 +327,6 @@ __global__ void __launch_bounds__(kThreads)
     s_part[p] = 0.0;
   }
   __syncthreads();
-  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   int buf = 0, cur = -1, p = 0;
   double acc = 0.0;
   for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -213,57 +341,10 @@ __global__ void __launch_bounds__(kThreads)
     }
     if (!s_active[p]) continue;
     const CGDesc<T>& d = descs[p];
-    const Grid3 g = d.g;
     const CGState& S = st[d.slot];
-    const bool first = S.first != 0;
-    const T beta = (T)S.beta;
     const int it = S.iter;
-    const T* __restrict__ r = d.r;
-    const T* __restrict__ pold = (it & 1) ? d.pb : d.pa;
-    T* __restrict__ pnew = (it & 1) ? d.pa : d.pb;
-    T* __restrict__ q = d.q;
-    const TileXYZ c = tile_coords(g, d.t, t - d.tile_begin);
-    const int i = c.x0 + tx, j = c.y0 + ty;
-    const bool own = (i <= g.nx) && (j <= g.ny);
-    const bool inxy = (i > 0) && (i < g.nx) && (j > 0) && (j < g.ny);
-    const T c0 = (T)d.A.c0, fx = (T)d.A.fx, fy = (T)d.A.fy, fz = (T)d.A.fz;
-    const T exy = (T)d.A.exy, exz = (T)d.A.exz, eyz = (T)d.A.eyz;
-    T Pm1 = T(0), Cm1 = T(0), Tm1 = T(0), Tm2 = T(0), tacc = T(0);
-    for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
-      const bool plane_in = (kk >= 0) && (kk <= g.nz);
-      for (int idx = threadIdx.x; idx < (kTX + 2) * (kTY + 2); idx += kThreads) {
-        const int ly = idx / (kTX + 2), lx = idx - ly * (kTX + 2);
-        const int gi = c.x0 - 1 + lx, gj = c.y0 - 1 + ly;
-        T v = T(0);
-        if (plane_in && gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny) {
-          const long long o = gi + gj * g.sy + (long long)kk * g.sz;
-          v = first ? r[o] : fmaT(beta, pold[o], r[o]);
-        }
-        sp[buf][ly][lx] = v;
-      }
-      __syncthreads();
-      const T P = sp[buf][ty + 1][tx + 1];
-      const T SX = sp[buf][ty + 1][tx] + sp[buf][ty + 1][tx + 2];
-      const T SY = sp[buf][ty][tx + 1] + sp[buf][ty + 2][tx + 1];
-      const T EXY = (sp[buf][ty][tx] + sp[buf][ty][tx + 2]) + (sp[buf][ty + 2][tx] + sp[buf][ty + 2][tx + 2]);
-      const T Ck = fmaT(c0, P, fmaT(fx, SX, fmaT(fy, SY, exy * EXY)));
-      const T Tk = fmaT(fz, P, fmaT(exz, SX, eyz * SY));
-      const int kc = kk - 1;
-      if (kc >= c.z0 && own) {
-        const long long o = i + j * g.sy + (long long)kc * g.sz;
-        const bool interior = inxy && kc > 0 && kc < g.nz;
-        const T qv = interior ? (Cm1 + Tm2) + Tk : T(0);
-        pnew[o] = Pm1;
-        q[o] = qv;
-        tacc = fmaT(Pm1, qv, tacc);
-      }
-      Tm2 = Tm1;
-      Tm1 = Tk;
-      Cm1 = Ck;
-      Pm1 = P;
-      buf ^= 1;
-    }
-    acc += (double)tacc;
+    acc += (double)spmv_tile<T>(d, t - d.tile_begin, S.first != 0, (T)S.beta,
+                                (it & 1) ? d.pb : d.pa, (it & 1) ? d.pa : d.pb, sp, buf);
   }
   if (cur >= 0) {
     const double s = block_sum(acc);
@@ -287,7 +368,6 @@ __global__ void __launch_bounds__(kThreads)
     s_part[p] = 0.0;
   }
   __syncthreads();
-  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   int cur = -1, p = 0;
   double acc = 0.0;
   for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -302,29 +382,9 @@ __global__ void __launch_bounds__(kThreads)
     }
     if (!s_active[p]) continue;
     const CGDesc<T>& d = descs[p];
-    const Grid3 g = d.g;
     const CGState& S = st[d.slot];
-    const T alpha = (T)S.alpha;
     const int it = S.iter;
-    const T* __restrict__ pn = (it & 1) ? d.pa : d.pb;
-    const T* __restrict__ q = d.q;
-    T* __restrict__ x = d.x;
-    T* __restrict__ r = d.r;
-    const TileXYZ c = tile_coords(g, d.t, t - d.tile_begin);
-    const int i = c.x0 + tx, j = c.y0 + ty;
-    T tacc = T(0);
-    if (i <= g.nx && j <= g.ny) {
-      long long o = i + j * g.sy + (long long)c.z0 * g.sz;
-#pragma unroll 4
-      for (int k = c.z0; k < c.z1; ++k, o += g.sz) {
-        const T xv = fmaT(alpha, pn[o], x[o]);
-        const T rv = fmaT(-alpha, q[o], r[o]);
-        x[o] = xv;
-        r[o] = rv;
-        tacc = fmaT(rv, rv, tacc);
-      }
-    }
-    acc += (double)tacc;
+    acc += (double)update_tile<T>(d, t - d.tile_begin, (T)S.alpha, (it & 1) ? d.pa : d.pb);
   }
   if (cur >= 0) {
     const double s = block_sum(acc);
@@ -335,6 +395,136 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------------
+// Persistent CG: every CG step of one problem in one cooperative launch.  Each step
+// runs the K1 body over the block's tiles, a grid-wide reduction of p.q, the K2 body,
+// and a grid-wide reduction of r.r.  A reduction is: each block writes its partial,
+// one grid barrier, then every block sums all partials in index order -- so every
+// block derives bit-identical alpha, beta and the same stopping decision, and no
+// second barrier or broadcast is needed.  Barrier waits are bounded: on time-out the
+// kernel records EXCMG_ERR_TIMEOUT and returns.
+// ---------------------------------------------------------------------------------
+constexpr unsigned long long kSpinLimit = 1ull << 24;  // x >= 64 ns: about a second or more
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Every block arrives once; returns false in every block that saw a time-out.
+__device__ bool grid_barrier(unsigned* bar, unsigned target, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    unsigned long long spins = 0;
+    while (ld_acquire(bar) < target) {
+      if (++spins > kSpinLimit || *(volatile int*)err) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (!ok) atomicExch(err, 1);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Sum of n partials in index order, identical in every block.  Result in thread 0.
+__device__ double sum_partials_all(const double* part, int n) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += __ldcg(part + i);
+  return block_sum(acc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_cg_persistent(const CGDesc<T>* __restrict__ descs, long long total_tiles, CGState* st,
+                    double* partials, unsigned* bar, int* err) {
+  __shared__ T sp[2][kTY + 2][kTX + 2];
+  __shared__ double s_scalar;
+  const CGDesc<T>& d = descs[0];
+  CGState* S = st + d.slot;
+  if (S->done) return;  // same value in every block: nothing to do
+  const int G = gridDim.x;
+  double* partA = partials;
+  double* partB = partials + G;
+  double rr = S->rr, beta = S->beta, tol2 = S->tol2, pq = 0.0, alpha = 0.0;
+  int iter = S->iter;
+  const int max_iter = S->max_iter, fixed = S->fixed;
+  bool first = S->first != 0;
+  int status = EXCMG_OK;
+  unsigned nbar = 0;
+  int buf = 0;
+  for (;;) {
+    // K1 body
+    const T* pold = (iter & 1) ? d.pb : d.pa;
+    T* pnew = (iter & 1) ? d.pa : d.pb;
+    double acc = 0.0;
+    for (long long t = blockIdx.x; t < total_tiles; t += G)
+      acc += (double)spmv_tile<T>(d, t, first, (T)beta, pold, pnew, sp, buf);
+    double bs = block_sum(acc);
+    if (threadIdx.x == 0) partA[blockIdx.x] = bs;
+    if (!grid_barrier(bar, ++nbar * (unsigned)G, err)) {
+      status = EXCMG_ERR_TIMEOUT;
+      break;
+    }
+    bs = sum_partials_all(partA, G);
+    if (threadIdx.x == 0) s_scalar = bs;
+    __syncthreads();
+    pq = s_scalar;
+    if (pq == 0.0 && rr == 0.0) break;  // exact solution (fixed-count mode)
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      status = EXCMG_ERR_NONFINITE;
+      break;
+    }
+    alpha = rr / pq;
+    // K2 body
+    acc = 0.0;
+    for (long long t = blockIdx.x; t < total_tiles; t += G)
+      acc += (double)update_tile<T>(d, t, (T)alpha, pnew);
+    bs = block_sum(acc);
+    if (threadIdx.x == 0) partB[blockIdx.x] = bs;
+    if (!grid_barrier(bar, ++nbar * (unsigned)G, err)) {
+      status = EXCMG_ERR_TIMEOUT;
+      break;
+    }
+    bs = sum_partials_all(partB, G);
+    if (threadIdx.x == 0) s_scalar = bs;
+    __syncthreads();
+    const double rrn = s_scalar;
+    beta = (rr > 0.0) ? rrn / rr : 0.0;
+    rr = rrn;
+    iter += 1;
+    first = false;
+    if (!isfinite(rr)) {
+      status = EXCMG_ERR_NONFINITE;
+      break;
+    }
+    if (rr <= tol2) break;
+    if (iter >= max_iter) {
+      if (!fixed) status = EXCMG_ERR_NOT_CONVERGED;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->rr = rr;
+    S->pq = pq;
+    S->alpha = alpha;
+    S->beta = beta;
+    S->iter = iter;
+    S->first = first ? 1 : 0;
+    S->status = status;
+    S->done = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // K3: r = LHS(u) - RHS(f) = b - A u_I (float64), sums r.r and b.b, CG state init
 // ---------------------------------------------------------------------------------
 template <typename TR>
@@ -342,7 +532,6 @@ __global__ void __launch_bounds__(kThreads)
     k_residual(int nprob, const ResDesc* __restrict__ descs, long long total_tiles,
                CGState* st, double* partials, unsigned* counters) {
   __shared__ double su[2][kTY + 2][kTX + 2];
-  __shared__ double sb[2][kTY + 2][kTX + 2];
   __shared__ int s_active[kMaxProb];
   __shared__ double s_part[2 * kMaxProb];
   for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
@@ -376,8 +565,14 @@ __global__ void __launch_bounds__(kThreads)
     const int i = c.x0 + tx, j = c.y0 + ty;
     const bool own = (i <= g.nx) && (j <= g.ny);
     const bool inxy = (i > 0) && (i < g.nx) && (j > 0) && (j < g.ny);
+    // interior columns next to an x or y boundary face: their lift has in-plane terms
+    const bool perim = inxy && (i == 1 || i == g.nx - 1 || j == 1 || j == g.ny - 1);
+    // which of the 3x3 neighbour columns are boundary columns
+    const bool bxm = (i - 1 == 0), bxp = (i + 1 == g.nx), bym = (j - 1 == 0), byp = (j + 1 == g.ny);
+    const bool want_b = d.want_b != 0;
     const Coef A = d.A;
-    // C/T terms of the stencil of u (all 19 nodes) and of its boundary part (the lift)
+    // C/T terms (see k_dir_spmv_dot) of the stencil of u over all 19 nodes, and of its
+    // boundary part: b = LHS(boundary part of u) - RHS(f)
     double Cm1 = 0, Tm1 = 0, Tm2 = 0, LCm1 = 0, LTm1 = 0, LTm2 = 0;
     for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
       const bool plane_in = (kk >= 0) && (kk <= g.nz);
@@ -385,32 +580,33 @@ __global__ void __launch_bounds__(kThreads)
       for (int idx = threadIdx.x; idx < (kTX + 2) * (kTY + 2); idx += kThreads) {
         const int ly = idx / (kTX + 2), lx = idx - ly * (kTX + 2);
         const int gi = c.x0 - 1 + lx, gj = c.y0 - 1 + ly;
-        double v = 0.0, vb = 0.0;
-        if (plane_in && gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny) {
+        double v = 0.0;
+        if (plane_in && gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny)
           v = u[gi + gj * g.sy + (long long)kk * g.sz];
-          const bool bnd = plane_bnd || gi == 0 || gi == g.nx || gj == 0 || gj == g.ny;
-          vb = bnd ? v : 0.0;
-        }
         su[buf][ly][lx] = v;
-        sb[buf][ly][lx] = vb;
       }
       __syncthreads();
-      double Ck, Tk, LCk, LTk;
-      {
-        const double P = su[buf][ty + 1][tx + 1];
-        const double SX = su[buf][ty + 1][tx] + su[buf][ty + 1][tx + 2];
-        const double SY = su[buf][ty][tx + 1] + su[buf][ty + 2][tx + 1];
-        const double EXY = (su[buf][ty][tx] + su[buf][ty][tx + 2]) + (su[buf][ty + 2][tx] + su[buf][ty + 2][tx + 2]);
-        Ck = fma(A.c0, P, fma(A.fx, SX, fma(A.fy, SY, A.exy * EXY)));
-        Tk = fma(A.fz, P, fma(A.exz, SX, A.eyz * SY));
-      }
-      {
-        const double P = sb[buf][ty + 1][tx + 1];
-        const double SX = sb[buf][ty + 1][tx] + sb[buf][ty + 1][tx + 2];
-        const double SY = sb[buf][ty][tx + 1] + sb[buf][ty + 2][tx + 1];
-        const double EXY = (sb[buf][ty][tx] + sb[buf][ty][tx + 2]) + (sb[buf][ty + 2][tx] + sb[buf][ty + 2][tx + 2]);
-        LCk = fma(A.c0, P, fma(A.fx, SX, fma(A.fy, SY, A.exy * EXY)));
-        LTk = fma(A.fz, P, fma(A.exz, SX, A.eyz * SY));
+      const double P = su[buf][ty + 1][tx + 1];
+      const double W = su[buf][ty + 1][tx], E = su[buf][ty + 1][tx + 2];
+      const double S = su[buf][ty][tx + 1], N = su[buf][ty + 2][tx + 1];
+      const double SW = su[buf][ty][tx], SE = su[buf][ty][tx + 2];
+      const double NW = su[buf][ty + 2][tx], NE = su[buf][ty + 2][tx + 2];
+      const double SX = W + E, SY = S + N, EXY = (SW + SE) + (NW + NE);
+      const double Ck = fma(A.c0, P, fma(A.fx, SX, fma(A.fy, SY, A.exy * EXY)));
+      const double Tk = fma(A.fz, P, fma(A.exz, SX, A.eyz * SY));
+      double LCk = 0.0, LTk = 0.0;
+      if (want_b) {
+        if (plane_bnd) {  // every node of a z-boundary plane is a boundary node
+          LCk = Ck;
+          LTk = Tk;
+        } else if (perim) {  // only the boundary columns of this plane
+          const double mSX = (bxm ? W : 0.0) + (bxp ? E : 0.0);
+          const double mSY = (bym ? S : 0.0) + (byp ? N : 0.0);
+          const double mEXY = ((bxm || bym) ? SW : 0.0) + ((bxp || bym) ? SE : 0.0) +
+                              ((bxm || byp) ? NW : 0.0) + ((bxp || byp) ? NE : 0.0);
+          LCk = fma(A.fx, mSX, fma(A.fy, mSY, A.exy * mEXY));
+          LTk = fma(A.exz, mSX, A.eyz * mSY);
+        }
       }
       const int kc = kk - 1;
       if (kc >= c.z0 && own) {
@@ -424,11 +620,13 @@ __global__ void __launch_bounds__(kThreads)
                     : 0.5 * (6.0 * F.at(i, j, kc) + ((F.at(i - 1, j, kc) + F.at(i + 1, j, kc)) +
                                                      (F.at(i, j - 1, kc) + F.at(i, j + 1, kc)) +
                                                      (F.at(i, j, kc - 1) + F.at(i, j, kc + 1))));
-          // LHS(u) = -(A-stencil of u over all 19 nodes); b = LHS(boundary part) - RHS
+          // LHS(u) = -(A-stencil of u over all 19 nodes)
           rv = -((Cm1 + Tm2) + Tk) - rhs;
-          const double bv = -((LCm1 + LTm2) + LTk) - rhs;
           acc_r = fma(rv, rv, acc_r);
-          acc_b = fma(bv, bv, acc_b);
+          if (want_b) {
+            const double bv = -((LCm1 + LTm2) + LTk) - rhs;
+            acc_b = fma(bv, bv, acc_b);
+          }
         }
         rout[o] = (TR)rv;
       }
@@ -466,16 +664,74 @@ __global__ void __launch_bounds__(kThreads)
     const int i = c.x0 + tx, j = c.y0 + ty;
     if (i > g.nx || j > g.ny) continue;
     long long o = i + j * g.sy + (long long)c.z0 * g.sz;
+    const double inv = 1.0 / d.scale;
     for (int k = c.z0; k < c.z1; ++k, o += g.sz) {
-      d.aux[o] += (double)d.x[o];
+      d.aux[o] += (double)d.x[o] * inv;
       d.x[o] = 0.0f;
     }
   }
 }
 
+// MIXED: r *= scale (in float64, then rounded); one thread per problem rescales r.r and
+// the inner tolerance of that problem's CG state.
+__global__ void __launch_bounds__(kThreads)
+    k_scale_rhs(int nprob, const CGDesc<float>* __restrict__ descs, long long total_tiles,
+                CGState* st) {
+  if (blockIdx.x == 0)
+    for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+      CGState& S = st[descs[p].slot];
+      const double s2 = descs[p].scale * descs[p].scale;
+      S.rr *= s2;
+      S.tol2 *= s2;
+    }
+  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+  int p = 0;
+  for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    p = find_problem(descs, nprob, t, p);
+    const CGDesc<float>& d = descs[p];
+    const Grid3 g = d.g;
+    const TileXYZ c = tile_coords(g, d.t, t - d.tile_begin);
+    const int i = c.x0 + tx, j = c.y0 + ty;
+    if (i > g.nx || j > g.ny) continue;
+    long long o = i + j * g.sy + (long long)c.z0 * g.sz;
+    for (int k = c.z0; k < c.z1; ++k, o += g.sz) d.r[o] = (float)((double)d.r[o] * d.scale);
+  }
+}
+
 int g_max_grid = 0;
+int g_coop_grid[2] = {0, 0};  // co-resident blocks of k_cg_persistent<double>, <float>
 
 }  // namespace
+
+template <typename T>
+int persistent_cg_blocks() {
+  int& cached = g_coop_grid[sizeof(T) == 8 ? 0 : 1];
+  if (cached == 0) {
+    int dev = 0, sms = 0, occ = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_persistent<T>, kThreads, 0);
+    cached = (coop && sms > 0 && occ > 0) ? std::min(sms * occ, kMaxGrid) : -1;
+  }
+  return cached;
+}
+template int persistent_cg_blocks<double>();
+template int persistent_cg_blocks<float>();
+
+template <typename T>
+cudaError_t launch_cg_persistent(const CGDesc<T>* descs, long long total_tiles, int grid,
+                                 CGState* st, double* partials, unsigned* bar, int* err,
+                                 cudaStream_t s) {
+  void* args[] = {(void*)&descs, (void*)&total_tiles, (void*)&st, (void*)&partials, (void*)&bar,
+                  (void*)&err};
+  return cudaLaunchCooperativeKernel((const void*)k_cg_persistent<T>, dim3(grid), dim3(kThreads),
+                                     args, 0, s);
+}
+template cudaError_t launch_cg_persistent<double>(const CGDesc<double>*, long long, int, CGState*,
+                                                  double*, unsigned*, int*, cudaStream_t);
+template cudaError_t launch_cg_persistent<float>(const CGDesc<float>*, long long, int, CGState*,
+                                                 double*, unsigned*, int*, cudaStream_t);
 
 int persistent_grid(long long total_tiles) {
   if (g_max_grid == 0) {
@@ -523,6 +779,12 @@ cudaError_t launch_residual(bool out_float, int nprob, const ResDesc* descs, lon
 cudaError_t launch_add_correction(int nprob, const CGDesc<float>* inner, long long total_tiles,
                                   int grid, cudaStream_t s) {
   k_add_correction<<<grid, kThreads, 0, s>>>(nprob, inner, total_tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_rhs(int nprob, const CGDesc<float>* inner, long long total_tiles,
+                             int grid, CGState* st, cudaStream_t s) {
+  k_scale_rhs<<<grid, kThreads, 0, s>>>(nprob, inner, total_tiles, st);
   return cudaGetLastError();
 }
 

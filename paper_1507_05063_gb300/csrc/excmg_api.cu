@@ -47,13 +47,15 @@ Tiling make_tiling(const Grid3& g, int tz) {
   return t;
 }
 
-// Slab depth: among 4..64 the one minimising (waves of tiles) x (planes staged per tile),
-// a model of the stencil kernel's time when every block runs at the same rate.
+// Slab depth: among 1..64 the one minimising (waves of tiles) x (planes staged per tile),
+// a model of the stencil kernel's time when every block runs at the same rate.  Large
+// grids get deep slabs (little halo re-staging); small, latency-bound grids get thin
+// slabs and so more tiles in flight.
 int choose_tz(const Grid3& g, int grid_blocks, int requested) {
   if (requested > 0) return requested;
   int best = 16;
   double best_cost = 1e300;
-  const int cands[] = {4, 6, 8, 12, 16, 24, 32, 48, 64};
+  const int cands[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
   for (int tz : cands) {
     const Tiling t = make_tiling(g, tz);
     const long long tiles = t.count();
@@ -167,17 +169,22 @@ ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_
 
 // Common header of every workspace: states, counters, partials, descriptor tables.
 struct Header {
-  size_t st, counters, partials, cgd, cgf, resd, prold;
+  size_t st, counters, bar, partials, cgd, cgf, resd, prold;
   size_t bytes;
 };
+
+// States: one per problem of a batch, or one per level of a single solve.
+int state_slots(int nprob) { return std::max(nprob, (int)EXCMG_MAX_LEVELS); }
 
 Header header_layout(int nprob) {
   Header H;
   size_t off = 0;
   H.st = off;
-  off = align_up(off + sizeof(CGState) * nprob);
+  off = align_up(off + sizeof(CGState) * state_slots(nprob));
   H.counters = off;
-  off = align_up(off + sizeof(unsigned) * nprob);
+  off = align_up(off + sizeof(unsigned) * state_slots(nprob));
+  H.bar = off;  // grid-barrier arrival count (unsigned) + time-out flag (int)
+  off = align_up(off + 2 * sizeof(unsigned));
   H.partials = off;
   off = align_up(off + sizeof(double) * 2 * (size_t)nprob * kMaxGrid);
   H.cgd = off;
@@ -232,6 +239,7 @@ struct Prof {
     size_t e0, e1;   // indices into pool
     double nodes;
     bool real;
+    int iter_slot;   // >= 0: nodes are per CG step, times the steps of that state slot
   };
   std::vector<cudaEvent_t> pool;
   std::vector<Rec> recs;
@@ -245,15 +253,21 @@ struct Prof {
     return pool.size() - 1;
   }
   // Sum the records into stats after the stream has been synchronised.
-  void report(excmg_stats* st) const {
+  void report(excmg_stats* st, const std::vector<CGState>& states) const {
     if (!st) return;
     for (const Rec& r : recs) {
       if (!r.real || !pool[r.e0] || !pool[r.e1]) continue;
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, pool[r.e0], pool[r.e1]) != cudaSuccess) continue;
+      double nodes = r.nodes;
+      if (r.iter_slot >= 0) {
+        const int steps = r.iter_slot < (int)states.size() ? states[r.iter_slot].iter : 0;
+        if (steps <= 0) continue;
+        nodes *= steps;
+      }
       st->prof_ms[r.kind] += ms;
       st->prof_launches[r.kind] += 1;
-      st->prof_nodes[r.kind] += r.nodes;
+      st->prof_nodes[r.kind] += nodes;
     }
   }
 };
@@ -264,6 +278,8 @@ struct Ctx {
   cudaStream_t s;
   long long* launches = nullptr;  // kernels launched by this call
   Prof* prof = nullptr;           // set when the call is profiled
+  bool persistent_ok = false;     // single-problem CG may use the cooperative kernel
+  bool defer = false;             // the caller reads the CG states after the whole call
   // Bracket one launch: record an event before `fn` and after it.
   template <typename F>
   cudaError_t timed(int kind, double nodes, F fn) const {
@@ -273,11 +289,13 @@ struct Ctx {
     if (prof->pool[a]) cudaEventRecord(prof->pool[a], s);
     cudaError_t e = fn();
     if (prof->pool[b]) cudaEventRecord(prof->pool[b], s);
-    prof->recs.push_back({kind, a, b, nodes, true});
+    prof->recs.push_back({kind, a, b, nodes, true, -1});
     return e;
   }
   CGState* st() const { return reinterpret_cast<CGState*>(ws + H.st); }
   unsigned* counters() const { return reinterpret_cast<unsigned*>(ws + H.counters); }
+  unsigned* bar() const { return reinterpret_cast<unsigned*>(ws + H.bar); }
+  int* bar_err() const { return reinterpret_cast<int*>(ws + H.bar + sizeof(unsigned)); }
   double* partials() const { return reinterpret_cast<double*>(ws + H.partials); }
   CGDesc<double>* cgd() const { return reinterpret_cast<CGDesc<double>*>(ws + H.cgd); }
   CGDesc<float>* cgf() const { return reinterpret_cast<CGDesc<float>*>(ws + H.cgf); }
@@ -298,6 +316,28 @@ template <typename T>
 excmg_status cg_loop(const Ctx& c, int n, const CGDesc<T>* ddesc, long long tiles, int grid,
                      const std::vector<int>& slots, int nslots, int chunk0,
                      std::vector<CGState>& hs, double nodes) {
+  // A single problem runs all its steps in one cooperative launch when the device
+  // supports it and the barrier count cannot wrap.
+  if (n == 1) {
+    const int coop = persistent_cg_blocks<T>();
+    if (coop > 0 && c.persistent_ok) {
+      const int g = (int)std::min<long long>(tiles, coop);
+      CK(cudaMemsetAsync(c.bar(), 0, 2 * sizeof(unsigned), c.s));
+      const int kind = sizeof(T) == 8 ? EXCMG_K_CG_F64 : EXCMG_K_CG_F32;
+      if (c.launches) *c.launches += 1;
+      if (c.prof) {
+        const size_t a = c.prof->event(), b = c.prof->event();
+        if (c.prof->pool[a]) cudaEventRecord(c.prof->pool[a], c.s);
+        CK(launch_cg_persistent<T>(ddesc, tiles, g, c.st(), c.partials(), c.bar(), c.bar_err(), c.s));
+        if (c.prof->pool[b]) cudaEventRecord(c.prof->pool[b], c.s);
+        c.prof->recs.push_back({kind, a, b, nodes, true, slots[0]});
+      } else {
+        CK(launch_cg_persistent<T>(ddesc, tiles, g, c.st(), c.partials(), c.bar(), c.bar_err(), c.s));
+      }
+      if (c.defer) return EXCMG_OK;
+      return read_states(c, nslots, hs);
+    }
+  }
   int chunk = chunk0 > 0 ? chunk0 : 4;
   Prof* prof = (c.prof && n == 1) ? c.prof : nullptr;
   const int kspmv = sizeof(T) == 8 ? EXCMG_K_SPMV_F64 : EXCMG_K_SPMV_F32;
@@ -310,8 +350,8 @@ excmg_status cg_loop(const Ctx& c, int n, const CGDesc<T>* ddesc, long long tile
         const size_t e0 = prof->event(), e1 = prof->event(), e2 = prof->event();
         CK(launch_cg_step<T>(n, ddesc, tiles, grid, c.st(), c.partials(), c.counters(), c.s,
                              prof->pool[e0], prof->pool[e1], prof->pool[e2]));
-        prof->recs.push_back({kspmv, e0, e1, nodes, true});
-        prof->recs.push_back({kupd, e1, e2, nodes, true});
+        prof->recs.push_back({kspmv, e0, e1, nodes, true, -1});
+        prof->recs.push_back({kupd, e1, e2, nodes, true, -1});
       } else {
         CK(launch_cg_step<T>(n, ddesc, tiles, grid, c.st(), c.partials(), c.counters(), c.s));
       }
@@ -418,6 +458,7 @@ excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_opt
     }));
     excmg_status e = cg_loop<double>(c, n, c.cgd(), tiles, grid, slots, nslots, o->chunk, hs, nodes_sum);
     if (e != EXCMG_OK) return e;
+    if (c.defer) return EXCMG_OK;  // the caller reads every state at the end
     for (auto& it : items) {
       const CGState& S = hs[it.d64.slot];
       it.iters = S.iter;
@@ -470,6 +511,11 @@ excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_opt
       CGDesc<float> d = items[a].d32;
       d.tile_begin = ft;
       ft += d.t.count();
+      // scale r to unit root-mean-square over the interior unknowns
+      const double rr = hs[d.slot].rr;
+      const double nint = (double)(d.g.nx - 1) * (d.g.ny - 1) * (d.g.nz - 1);
+      d.scale = (rr > 0.0 && nint > 0.0) ? 1.0 / sqrt(rr / nint) : 1.0;
+      if (!isfinite(d.scale) || d.scale <= 0.0) d.scale = 1.0;
       fd.push_back(d);
       fslots.push_back(d.slot);
     }
@@ -478,6 +524,7 @@ excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_opt
     double fnodes = 0.0;
     for (int a : next) fnodes += (double)items[a].nodes;
     CK(cudaMemcpyAsync(c.cgf(), fd.data(), sizeof(CGDesc<float>) * nf, cudaMemcpyHostToDevice, c.s));
+    CK(c.timed(EXCMG_K_CORRECT, fnodes, [&] { return launch_scale_rhs(nf, c.cgf(), ft, fgrid, c.st(), c.s); }));
     e = cg_loop<float>(c, nf, c.cgf(), ft, fgrid, fslots, nslots, o->chunk, hs, fnodes);
     if (e != EXCMG_OK) return e;
     for (int a : next) {
@@ -521,6 +568,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   f.pb = reinterpret_cast<float*>(p.base + p.L.pb32);
   f.q = reinterpret_cast<float*>(p.base + p.L.q32);
   f.aux = p.level_u(l);
+  f.scale = 1.0;
   return it;
 }
 
@@ -535,6 +583,13 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
   c.launches = &launches;
   Prof prof;
   if (o->profile && np == 1) c.prof = &prof;
+  // a single solve keeps one CG state per level and reads them all at the end
+  const bool single = np == 1;
+  long long max_count = o->max_iter;
+  if (o->fixed_iters)
+    for (size_t l = 0; l < P[0].lv.size(); ++l) max_count = std::max<long long>(max_count, o->fixed_iters[l]);
+  c.persistent_ok = single && (long long)kMaxGrid * (2 * max_count + 4) < (1LL << 32);
+  c.defer = single && o->precision == EXCMG_FP64;
   struct Report {
     excmg_stats* st;
     long long* n;
@@ -602,11 +657,13 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
     std::vector<Item> items;
     std::vector<int> fixed;
     for (int a = 0; a < na; ++a) {
-      items.push_back(make_item(P[act[a]], lev[a], act[a], o));
+      items.push_back(make_item(P[act[a]], lev[a], single ? lev[a] : act[a], o));
       if (o->fixed_iters) fixed.push_back(o->fixed_iters[lev[a]]);
     }
-    excmg_status e = solve_items(c, items, o, np, o->fixed_iters ? fixed.data() : nullptr);
+    excmg_status e = solve_items(c, items, o, single ? state_slots(1) : np,
+                                 o->fixed_iters ? fixed.data() : nullptr);
     if (e != EXCMG_OK) return e;
+    if (c.defer) continue;
     for (int a = 0; a < na; ++a) {
       const Item& it = items[a];
       if (stats) {
@@ -627,7 +684,23 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
   }
   CK(cudaStreamSynchronize(c.s));
   CK(cudaGetLastError());
-  if (c.prof) prof.report(stats);
+  std::vector<CGState> hs;
+  if (c.defer || c.prof) {
+    excmg_status e = read_states(c, state_slots(np), hs);
+    if (e != EXCMG_OK) return e;
+  }
+  if (c.defer) {
+    for (int l = 0; l < (int)P[0].lv.size(); ++l) {
+      const CGState& S = hs[l];
+      if (stats) {
+        stats[0].iters[l] = S.iter;
+        stats[0].relres[l] = S.bb > 0 ? sqrt(S.rr / S.bb) : 0.0;
+      }
+      if (S.status != EXCMG_OK && (result == EXCMG_OK || S.status == EXCMG_ERR_NONFINITE))
+        result = (excmg_status)S.status;
+    }
+  }
+  if (c.prof) prof.report(stats, hs);
   return result;
 }
 
@@ -828,14 +901,19 @@ excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_optio
   Prof prof;
   c.launches = &launches;
   if (opt->profile) c.prof = &prof;
+  const long long max_count = opt->fixed_iters ? std::max(opt->max_iter, opt->fixed_iters[0]) : opt->max_iter;
+  c.persistent_ok = (long long)kMaxGrid * (2 * max_count + 4) < (1LL << 32);
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
   excmg_status e = solve_items(c, items, opt, 1, opt->fixed_iters);
   if (e != EXCMG_OK) return e;
   CK(cudaStreamSynchronize(c.s));
+  std::vector<CGState> hs;
+  e = read_states(c, 1, hs);
+  if (e != EXCMG_OK) return e;
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->launches = launches;
-    prof.report(stats);
+    prof.report(stats, hs);
     stats->levels = 1;
     stats->N[0][0] = lv[l].nx;
     stats->N[0][1] = lv[l].ny;
@@ -912,6 +990,7 @@ excmg_status excmg_adjoint(const excmg_grid* grid, const double* dLdu, const exc
   p.u = lam;
   p.base = c.ws + c.H.bytes + align_up(sizeof(double) * nf);
   p.L = prob_layout(p.lv, opt->precision == EXCMG_MIXED, false);
+  c.persistent_ok = (long long)kMaxGrid * (2LL * opt->max_iter + 4) < (1LL << 32);
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
   CK(cudaMemsetAsync(lam, 0, sizeof(double) * nf, c.s));
   Item it = make_item(p, 0, 0, opt);

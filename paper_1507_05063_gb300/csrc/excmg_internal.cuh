@@ -83,7 +83,9 @@ struct CGDesc {
   T* pa;                  // p buffers: even steps read pa and write pb, odd steps swap
   T* pb;
   T* q;
-  double* aux;            // MIXED inner solve: the float64 level solution u += x
+  double* aux;            // MIXED inner solve: the float64 level solution u += x / scale
+  double scale;           // MIXED inner solve: it solves A x = scale * r (r scaled to O(1)
+                          // so float32 products neither underflow nor overflow)
 };
 
 // One problem of a residual phase: r = LHS(u) - RHS(f) (= b - A u_I) in float64,
@@ -119,7 +121,23 @@ cudaError_t launch_residual(bool out_float, int nprob, const ResDesc* descs,
                             unsigned* counters, cudaStream_t s);
 cudaError_t launch_add_correction(int nprob, const CGDesc<float>* inner, long long total_tiles,
                                   int grid, cudaStream_t s);
+// MIXED: r *= scale on every problem's float32 residual, and the CG state's r.r and
+// tolerance by scale^2 (before the inner solve).
+cudaError_t launch_scale_rhs(int nprob, const CGDesc<float>* inner, long long total_tiles,
+                             int grid, CGState* st, cudaStream_t s);
 int persistent_grid(long long total_tiles);
+
+// All CG steps of ONE problem in one cooperative launch (grid barriers with bounded
+// waits; EXCMG_ERR_TIMEOUT in the state if a wait runs out).  `bar` (zeroed before the
+// launch) counts barrier arrivals, `err` (zeroed) flags a time-out; `partials` needs 2 x
+// grid doubles.  persistent_cg_blocks() is the largest co-resident grid, or -1 if the
+// device has no cooperative launch.
+template <typename T>
+int persistent_cg_blocks();
+template <typename T>
+cudaError_t launch_cg_persistent(const CGDesc<T>* descs, long long total_tiles, int grid,
+                                 CGState* st, double* partials, unsigned* bar, int* err,
+                                 cudaStream_t s);
 
 // Transfer kernels (transfer_kernels.cu).
 struct ProlongDesc {

@@ -26,7 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 MAX_LEVELS = 24
 FP64, MIXED = 0, 1
 KERNEL_NAMES = ["spmv_f64", "update_f64", "spmv_f32", "update_f32", "residual", "exp_finite",
-                "init", "correct", "exp_true"]
+                "init", "correct", "exp_true", "cg_f64", "cg_f32"]
 KERNEL_KINDS = len(KERNEL_NAMES)
 STATUS = {0: "EXCMG_OK", 1: "EXCMG_ERR_INVALID_ARG", 2: "EXCMG_ERR_NOT_CONVERGED",
           3: "EXCMG_ERR_CUDA", 4: "EXCMG_ERR_NONFINITE", 5: "EXCMG_ERR_TIMEOUT",
@@ -278,7 +278,8 @@ class BatchedProblem:
     g: torch.Tensor
 
 
-def solve_batched(problems: List[BatchedProblem], stream=None, ws=None, **opts):
+def solve_batched(problems: List[BatchedProblem], stream=None, ws=None, allow_not_converged=False,
+                  **opts):
     n = len(problems)
     grids = (Grid * n)(*[make_grid(p.L, p.N, p.N0) for p in problems])
     o, _keep = make_options(**opts)
@@ -295,7 +296,7 @@ def solve_batched(problems: List[BatchedProblem], stream=None, ws=None, **opts):
     st = (Stats * n)()
     status = excmg_solve_batched(n, grids, fp, gp, ctypes.byref(o), up, _ptr(ws), ws.numel(),
                                  st, _stream(stream))
-    _check(status, "excmg_solve_batched")
+    _check(status, "excmg_solve_batched", allow=(2,) if allow_not_converged else ())
     return {"u": us, "stats": [s.to_dict() for s in st], "status": STATUS[status]}
 
 
