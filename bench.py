@@ -66,18 +66,23 @@ ALGO = {
     # persistent CG: per node and CG step (the two fused bodies above)
     "cg_f64": {"bytes": 80.0, "dp_ops": 19.0},
     "cg_f32": {"bytes": 40.0, "dp_ops": 0.0},
+    # single-block CG of a small grid: vectors live in shared memory
+    "cg_small_f64": {"bytes": 0.0, "dp_ops": 30.0},
+    "cg_small_f32": {"bytes": 0.0, "dp_ops": 0.0},
 }
 KERNEL_SYMBOL = {"spmv_f64": "k_dir_spmv_dot<double>", "update_f64": "k_update_dot<double>",
                  "spmv_f32": "k_dir_spmv_dot<float>", "update_f32": "k_update_dot<float>",
                  "residual": "k_residual", "exp_finite": "k_exp_finite", "init": "k_boundary_init",
                  "correct": "k_add_correction", "exp_true": "k_exp_true",
-                 "cg_f64": "k_cg_persistent<double>", "cg_f32": "k_cg_persistent<float>"}
+                 "cg_f64": "k_cg_persistent<double>", "cg_f32": "k_cg_persistent<float>",
+                 "cg_small_f64": "k_cg_small<double>", "cg_small_f32": "k_cg_small<float>"}
 KERNEL_SOURCE = {"spmv_f64": "cg_kernels.cu", "update_f64": "cg_kernels.cu",
                  "spmv_f32": "cg_kernels.cu", "update_f32": "cg_kernels.cu",
                  "residual": "cg_kernels.cu", "exp_finite": "transfer_kernels.cu",
                  "init": "transfer_kernels.cu", "correct": "cg_kernels.cu",
                  "exp_true": "transfer_kernels.cu", "cg_f64": "cg_kernels.cu",
-                 "cg_f32": "cg_kernels.cu"}
+                 "cg_f32": "cg_kernels.cu", "cg_small_f64": "cg_kernels.cu",
+                 "cg_small_f32": "cg_kernels.cu"}
 # FP64 issue rate: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz (maximum SM clock).
 DP_PEAK_GOPS = 2 * 152 * 2.070
 
@@ -209,12 +214,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c4", "c5"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip mixed / CG-rate extras")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload in ("c4", "c5"):
+        {"c4": run_batched, "c5": run_adjoint}[args.workload](args)
         return
 
     import torch
@@ -372,6 +380,91 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _setup_gpu():
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1507_05063_gb300 import excmg as X
+    return torch, X
+
+
+def run_batched(args):
+    """64 independent problems (sizes from {32,64,128,256}^3 cells, random aspect),
+    solved together by excmg_solve_batched; MIXED (float32 inner solves, float64
+    refinement) and FP64.  value = interior unknowns of all problems per second."""
+    torch, X = _setup_gpu()
+    seed, nprob, eps = 20151507, 64, 1e-8
+    grids = P.batched_grids(nprob, seed)
+    probs, n_unk = [], 0
+    for i, (L, N, N0) in enumerate(grids):
+        f, g, u = P.make_inputs(P.trig_sum(seed + i, K=8, L=L), N, L)
+        probs.append((L, N, N0, f, g, u))
+        n_unk += interior_unknowns(N)
+    batch = [X.BatchedProblem(L, N, N0, torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda())
+             for L, N, N0, f, g, _ in probs]
+    out = {"metric": METRIC, "unit": "unknowns/s", "workload": "batched", "n_problems": nprob,
+           "unknowns": n_unk, "eps": eps, "sizes": [list(p[1]) for p in probs]}
+    for prec in ("mixed", "fp64"):
+        for _ in range(max(1, args.warmup)):
+            res = X.solve_batched(batch, eps=eps, precision=prec, eps_coarse=1e-10)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(1, args.steps // 4)
+        a.record()
+        for _ in range(k):
+            res = X.solve_batched(batch, eps=eps, precision=prec, eps_coarse=1e-10)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / k
+        errs = [float(np.max(np.abs(u.cpu().numpy() - p[5]))) / max(float(np.max(np.abs(p[5]))), 1e-300)
+                for u, p in zip(res["u"], probs)]
+        out[prec] = {"value": n_unk / (ms / 1e3), "ms_per_batch": ms, "status": res["status"],
+                     "max_rel_err_vs_exact": max(errs),
+                     "max_relres_finest": max(st["relres"][-1] for st in res["stats"])}
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint(args):
+    """Source recovery on a 256^3 cube: L = ||u(f) - u_t||^2 with u_t the solution for a
+    seeded trig-sum source; 20 gradient steps on f with dL/df from excmg_adjoint through
+    torch.autograd and an exact line search (L is quadratic in f)."""
+    torch, X = _setup_gpu()
+    from paper_1507_05063_gb300.autograd import excmg_solve
+    N, N0, L = (256, 256, 256), (4, 4, 4), (1.0, 1.0, 1.0)
+    ft, g, _ = P.make_inputs(P.trig_sum(20150705, K=8), N)
+    gd = torch.from_numpy(g).cuda()
+    out = {"metric": METRIC, "workload": "adjoint source recovery 256^3", "steps": 20}
+    for prec in ("fp64", "mixed"):
+        kw = dict(eps=1e-10, eps_coarse=1e-12, precision=prec)
+        ut = X.solve(torch.from_numpy(ft).cuda(), gd, L, N0, **kw)["u"]
+        f = torch.zeros_like(ut)
+        losses, t_fwd, t_adj = [], 0.0, 0.0
+        t0 = time.perf_counter()
+        for _ in range(20):
+            f.requires_grad_(True)
+            a = time.perf_counter()
+            u = excmg_solve(f, gd, L, N0, **kw)
+            loss = ((u - ut) ** 2).sum()
+            torch.cuda.synchronize()
+            t_fwd += time.perf_counter() - a
+            a = time.perf_counter()
+            loss.backward()
+            torch.cuda.synchronize()
+            t_adj += time.perf_counter() - a
+            d = f.grad.detach()
+            with torch.no_grad():
+                Jd = X.solve(d, gd, L, N0, **kw)["u"] - X.solve(torch.zeros_like(d), gd, L, N0, **kw)["u"]
+                t = float(((u - ut).detach() * Jd).sum() / (Jd * Jd).sum())
+                f = f.detach() - t * d
+            losses.append(float(loss.detach()))
+        total = time.perf_counter() - t0
+        out[prec] = {"loss_first": losses[0], "loss_last": losses[-1],
+                     "monotone": all(b < a for a, b in zip(losses, losses[1:])),
+                     "seconds_total": total, "seconds_forward": t_fwd, "seconds_adjoint": t_adj}
+    print(json.dumps(out), flush=True)
 
 
 def extras(X, torch, device, L, N, N0, fd, gd, u_exact, opts, err_l2, err_linf, hbm_peak, args,

@@ -68,7 +68,9 @@ typedef enum {
   EXCMG_K_CG_F64 = 9,     /* all CG steps of a level in one persistent launch (float64);
                              prof_nodes counts nodes x steps */
   EXCMG_K_CG_F32 = 10,    /* the same for a float32 inner solve */
-  EXCMG_KERNEL_KINDS = 11
+  EXCMG_K_CG_SMALL_F64 = 11, /* all CG steps of a small grid in one block (float64) */
+  EXCMG_K_CG_SMALL_F32 = 12, /* the same in float32 */
+  EXCMG_KERNEL_KINDS = 13
 } excmg_kernel_kind;
 
 /* Box and grids (Section 2: hx = Lx/Nx ...; Algorithm 1: coarsest grid H, L levels). */
@@ -92,6 +94,9 @@ typedef struct {
                               many CG iterations on each level (FP64 only; parity tests) */
   int tile_z;              /* z-slab depth of the stencil kernels; 0 = library default */
   int chunk;               /* CG iterations enqueued between convergence reads; 0 = auto */
+  long long mixed_min_nodes; /* MIXED: grids with fewer nodes use float64 CG (latency-
+                              bound there, float32 saves nothing); 0 = library default
+                              2^21; 1 = float32 inner solves on every grid */
   int profile;             /* nonzero: time every kernel launch of excmg_solve / excmg_cg
                               with CUDA events on the caller's stream (stats.prof_*);
                               single-problem calls only; adds two event records per launch */
@@ -115,7 +120,8 @@ typedef struct {
 } excmg_stats;
 
 /* Writes the defaults: FP64, eps 1e-9, eps_coarse 1e-12, max_iter 100000,
-   inner_tol 1e-4, max_refine 50, fixed_iters NULL, tile_z 0, chunk 0, profile 0. */
+   inner_tol 1e-4, max_refine 50, fixed_iters NULL, tile_z 0, chunk 0,
+   mixed_min_nodes 0, profile 0. */
 void excmg_default_options(excmg_options* opt);
 
 /* Human-readable name of a status code (static string). */

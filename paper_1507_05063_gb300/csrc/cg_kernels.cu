@@ -36,16 +36,19 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Sum over the block; the result is valid in thread 0.  Every thread must call.
+// float64 instructions are scarce on this GPU (2 per clock per SM, 64-clock latency), so
+// only warp 0 adds: every thread parks its value in shared memory, then each lane of
+// warp 0 sums blockDim/32 of them in a fixed order and the warp reduces by shuffles.
+// The order is fixed, so the result is deterministic.
 __device__ double block_sum(double v) {
-  __shared__ double s_w[kThreads / 32];
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ double s_v[kThreads];
+  const int lane = threadIdx.x & 31;
   __syncthreads();
-  if (lane == 0) s_w[w] = v;
+  s_v[threadIdx.x] = v;
   __syncthreads();
   double t = 0.0;
-  if (w == 0) {
-    t = (lane < kThreads / 32) ? s_w[lane] : 0.0;
+  if (threadIdx.x < 32) {
+    for (int k = lane; k < (int)blockDim.x; k += 32) t += s_v[k];
     t = warp_sum(t);
   }
   return t;
@@ -102,8 +105,11 @@ __device__ void publish_and_finish(int nprob, const int* s_active, const double*
     for (int v = 0; v < NV; ++v) {
       double acc = 0.0;
       const volatile double* src = partials + ((long long)p * NV + v) * G;
-      for (int i = threadIdx.x; i < G; i += blockDim.x) acc += src[i];
-      sums[v] = block_sum(acc);
+      if (threadIdx.x < 32) {
+        for (int i = threadIdx.x; i < G; i += 32) acc += src[i];
+        acc = warp_sum(acc);
+      }
+      sums[v] = acc;
     }
     if (threadIdx.x == 0) {
       fin(p, sums);
@@ -435,15 +441,23 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* err) {
   return s_ok != 0;
 }
 
-// Sum of n partials in index order, identical in every block.  Result in thread 0.
+// Sum of n partials in a fixed order, identical in every block (warp 0 only: the adds
+// are float64).  Result in thread 0.
 __device__ double sum_partials_all(const double* part, int n) {
   double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += __ldcg(part + i);
-  return block_sum(acc);
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < n; i += 32) acc += __ldcg(part + i);
+    acc = warp_sum(acc);
+  }
+  return acc;
 }
 
+#ifndef EXCMG_PERSIST_MIN_BLOCKS
+#define EXCMG_PERSIST_MIN_BLOCKS 3
+#endif
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
     k_cg_persistent(const CGDesc<T>* __restrict__ descs, long long total_tiles, CGState* st,
                     double* partials, unsigned* bar, int* err) {
   __shared__ T sp[2][kTY + 2][kTX + 2];
@@ -698,6 +712,120 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Small-grid CG: one block holds x, r, p, q of the whole grid in shared memory and runs
+// every CG step with block barriers only (no global round trip per step).  Worth it
+// while one SM's float64 rate beats the multi-block kernel's per-step latency: grids
+// of up to kSmallNodes nodes.
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads)
+    k_cg_small(const CGDesc<T>* __restrict__ descs, CGState* st) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  __shared__ double s_red[1];
+  __shared__ double s_park[kSmallThreads];
+  const CGDesc<T>& d = descs[0];
+  CGState* S = st + d.slot;
+  if (S->done) return;
+  const Grid3 g = d.g;
+  const int n = (int)g.nodes();
+  T* xs = reinterpret_cast<T*>(s_raw);
+  T* rs = xs + n;
+  T* ps = rs + n;
+  T* qs = ps + n;
+  const int sy = (int)g.sy, sz = (int)g.sz;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) {
+    xs[o] = d.x[o];
+    rs[o] = d.r[o];
+    ps[o] = T(0);
+    qs[o] = T(0);
+  }
+  const T c0 = (T)d.A.c0, fx = (T)d.A.fx, fy = (T)d.A.fy, fz = (T)d.A.fz;
+  const T exy = (T)d.A.exy, exz = (T)d.A.exz, eyz = (T)d.A.eyz;
+  double rr = S->rr, beta = S->first ? 0.0 : S->beta, pq = 0.0, alpha = 0.0;
+  const double tol2 = S->tol2;
+  int iter = S->iter;
+  const int max_iter = S->max_iter, fixed = S->fixed;
+  int status = EXCMG_OK;
+  // block reduction: values parked in shared memory, float64 adds by warp 0 only, the
+  // result broadcast through shared memory (fixed order: deterministic)
+  auto reduce = [&](double v) -> double {
+    __syncthreads();
+    s_park[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int k = threadIdx.x; k < kSmallThreads; k += 32) t += s_park[k];
+      t = warp_sum(t);
+      if (threadIdx.x == 0) s_red[0] = t;
+    }
+    __syncthreads();
+    return s_red[0];
+  };
+  __syncthreads();
+  for (;;) {
+    for (int o = threadIdx.x; o < n; o += blockDim.x) ps[o] = fmaT((T)beta, ps[o], rs[o]);
+    __syncthreads();
+    double acc = 0.0;
+    for (int o = threadIdx.x; o < n; o += blockDim.x) {
+      const int i = o % sy, j = (o / sy) % (g.ny + 1), k = o / sz;
+      T qv = T(0);
+      if (i > 0 && i < g.nx && j > 0 && j < g.ny && k > 0 && k < g.nz) {
+        const T* P = ps + o;
+        const T SX = P[-1] + P[1], SY = P[-sy] + P[sy], SZ = P[-sz] + P[sz];
+        const T EXY = (P[-1 - sy] + P[1 - sy]) + (P[-1 + sy] + P[1 + sy]);
+        const T EXZ = (P[-1 - sz] + P[1 - sz]) + (P[-1 + sz] + P[1 + sz]);
+        const T EYZ = (P[-sy - sz] + P[sy - sz]) + (P[-sy + sz] + P[sy + sz]);
+        qv = fmaT(c0, P[0], fmaT(fx, SX, fmaT(fy, SY, fmaT(fz, SZ, fmaT(exy, EXY, fmaT(exz, EXZ, eyz * EYZ))))));
+        acc += (double)(P[0] * qv);
+      }
+      qs[o] = qv;
+    }
+    pq = reduce(acc);
+    if (pq == 0.0 && rr == 0.0) break;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      status = EXCMG_ERR_NONFINITE;
+      break;
+    }
+    alpha = rr / pq;
+    acc = 0.0;
+    for (int o = threadIdx.x; o < n; o += blockDim.x) {
+      xs[o] = fmaT((T)alpha, ps[o], xs[o]);
+      const T rv = fmaT((T)-alpha, qs[o], rs[o]);
+      rs[o] = rv;
+      acc += (double)(rv * rv);
+    }
+    const double rrn = reduce(acc);
+    beta = (rr > 0.0) ? rrn / rr : 0.0;
+    rr = rrn;
+    iter += 1;
+    if (!isfinite(rr)) {
+      status = EXCMG_ERR_NONFINITE;
+      break;
+    }
+    if (rr <= tol2) break;
+    if (iter >= max_iter) {
+      if (!fixed) status = EXCMG_ERR_NOT_CONVERGED;
+      break;
+    }
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < n; o += blockDim.x) {
+    d.x[o] = xs[o];
+    d.r[o] = rs[o];
+  }
+  if (threadIdx.x == 0) {
+    S->rr = rr;
+    S->pq = pq;
+    S->alpha = alpha;
+    S->beta = beta;
+    S->iter = iter;
+    S->first = 0;
+    S->status = status;
+    S->done = 1;
+  }
+}
+
 int g_max_grid = 0;
 int g_coop_grid[2] = {0, 0};  // co-resident blocks of k_cg_persistent<double>, <float>
 
@@ -718,6 +846,23 @@ int persistent_cg_blocks() {
 }
 template int persistent_cg_blocks<double>();
 template int persistent_cg_blocks<float>();
+
+template <typename T>
+cudaError_t launch_cg_small(const CGDesc<T>* descs, long long nodes, CGState* st, cudaStream_t s) {
+  const size_t smem = 4 * sizeof(T) * (size_t)nodes;
+  static bool attr_set[2] = {false, false};
+  bool& set = attr_set[sizeof(T) == 8 ? 0 : 1];
+  if (!set) {
+    cudaError_t e = cudaFuncSetAttribute(k_cg_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(4 * sizeof(T) * kSmallNodes));
+    if (e != cudaSuccess) return e;
+    set = true;
+  }
+  k_cg_small<T><<<1, kSmallThreads, smem, s>>>(descs, st);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cg_small<double>(const CGDesc<double>*, long long, CGState*, cudaStream_t);
+template cudaError_t launch_cg_small<float>(const CGDesc<float>*, long long, CGState*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_cg_persistent(const CGDesc<T>* descs, long long total_tiles, int grid,

@@ -120,7 +120,7 @@ bool options_ok(const excmg_options* o) {
   if (o->precision == EXCMG_MIXED && (!(o->inner_tol > 0) || !(o->inner_tol < 1) || o->max_refine < 1))
     return false;
   if (o->fixed_iters && o->precision != EXCMG_FP64) return false;
-  if (o->tile_z < 0 || o->tile_z > 256 || o->chunk < 0) return false;
+  if (o->tile_z < 0 || o->tile_z > 256 || o->chunk < 0 || o->mixed_min_nodes < 0) return false;
   return true;
 }
 
@@ -132,7 +132,12 @@ struct ProbLayout {
   size_t bytes;
 };
 
-ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_vectors) {
+long long mixed_min(const excmg_options* o) {
+  return o->mixed_min_nodes > 0 ? o->mixed_min_nodes : kMixedMinNodes;
+}
+
+ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_vectors,
+                       long long minn = kMixedMinNodes) {
   ProbLayout L;
   memset(&L, 0, sizeof(L));
   size_t off = 0;
@@ -141,15 +146,19 @@ ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_
     off = align_up(off + sizeof(double) * lv[l].nodes());
   }
   const long long nf = lv.back().nodes();
-  if (!mixed || need_fp64_vectors) {
+  // float64 CG vectors: every level (FP64), or the levels MIXED solves in float64
+  long long n64 = 0;
+  for (const Level& l : lv)
+    if (!mixed || need_fp64_vectors || l.nodes() < minn) n64 = std::max(n64, l.nodes());
+  if (n64 > 0) {
     L.r = off;
-    off = align_up(off + sizeof(double) * nf);
+    off = align_up(off + sizeof(double) * n64);
     L.pa = off;
-    off = align_up(off + sizeof(double) * nf);
+    off = align_up(off + sizeof(double) * n64);
     L.pb = off;
-    off = align_up(off + sizeof(double) * nf);
+    off = align_up(off + sizeof(double) * n64);
     L.q = off;
-    off = align_up(off + sizeof(double) * nf);
+    off = align_up(off + sizeof(double) * n64);
   }
   if (mixed) {
     L.r32 = off;
@@ -322,20 +331,35 @@ excmg_status cg_loop(const Ctx& c, int n, const CGDesc<T>* ddesc, long long tile
     const int coop = persistent_cg_blocks<T>();
     if (coop > 0 && c.persistent_ok) {
       const int g = (int)std::min<long long>(tiles, coop);
-      CK(cudaMemsetAsync(c.bar(), 0, 2 * sizeof(unsigned), c.s));
-      const int kind = sizeof(T) == 8 ? EXCMG_K_CG_F64 : EXCMG_K_CG_F32;
+      const bool small = nodes <= (double)kSmallNodes;
+      auto launch = [&]() -> cudaError_t {
+        if (small) return launch_cg_small<T>(ddesc, (long long)nodes, c.st(), c.s);
+        cudaError_t e = cudaMemsetAsync(c.bar(), 0, 2 * sizeof(unsigned), c.s);
+        if (e != cudaSuccess) return e;
+        return launch_cg_persistent<T>(ddesc, tiles, g, c.st(), c.partials(), c.bar(), c.bar_err(), c.s);
+      };
+      const int kind = small ? (sizeof(T) == 8 ? EXCMG_K_CG_SMALL_F64 : EXCMG_K_CG_SMALL_F32)
+                             : (sizeof(T) == 8 ? EXCMG_K_CG_F64 : EXCMG_K_CG_F32);
       if (c.launches) *c.launches += 1;
       if (c.prof) {
         const size_t a = c.prof->event(), b = c.prof->event();
         if (c.prof->pool[a]) cudaEventRecord(c.prof->pool[a], c.s);
-        CK(launch_cg_persistent<T>(ddesc, tiles, g, c.st(), c.partials(), c.bar(), c.bar_err(), c.s));
+        CK(launch());
         if (c.prof->pool[b]) cudaEventRecord(c.prof->pool[b], c.s);
         c.prof->recs.push_back({kind, a, b, nodes, true, slots[0]});
       } else {
-        CK(launch_cg_persistent<T>(ddesc, tiles, g, c.st(), c.partials(), c.bar(), c.bar_err(), c.s));
+        CK(launch());
       }
       if (c.defer) return EXCMG_OK;
-      return read_states(c, nslots, hs);
+      excmg_status e = read_states(c, nslots, hs);
+      if (e == EXCMG_OK && c.prof) {
+        // states are read now: count the steps before a later residual resets them
+        Prof::Rec& rec = c.prof->recs.back();
+        rec.nodes *= hs[slots[0]].iter;
+        rec.iter_slot = -1;
+        rec.real = hs[slots[0]].iter > 0;
+      }
+      return e;
     }
   }
   int chunk = chunk0 > 0 ? chunk0 : 4;
@@ -407,9 +431,34 @@ ResDesc make_res(const Grid3& g, const Tiling& t, int slot, const double* x, Vie
 // FP64: residual, then CG<double> until ||r|| <= eps ||b|| (fixed counts when
 // `fixed` is given).  MIXED: iterative refinement -- float64 residual r, float32 CG on
 // A e = r from e = 0 to inner_tol, x += e -- until ||r|| <= eps ||b||.
+excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excmg_options* o,
+                              int nslots, const int* fixed, bool mixed);
+
+// MIXED mode splits the systems: grids below kMixedMinNodes run the float64 CG,
+// larger ones the float32-inner refinement.
 excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_options* o,
                          int nslots, const int* fixed) {
-  const bool mixed = o->precision == EXCMG_MIXED;
+  if (o->precision != EXCMG_MIXED) return solve_items_impl(c, items, o, nslots, fixed, false);
+  const long long minn = mixed_min(o);
+  std::vector<Item> small, large;
+  std::vector<int> where;
+  for (auto& it : items) {
+    where.push_back(it.nodes < minn ? 0 : 1);
+    (it.nodes < minn ? small : large).push_back(it);
+  }
+  Ctx cs = c;
+  cs.defer = false;  // MIXED calls read their states per level
+  excmg_status e = solve_items_impl(cs, small, o, nslots, nullptr, false);
+  if (e != EXCMG_OK) return e;
+  e = solve_items_impl(cs, large, o, nslots, nullptr, true);
+  if (e != EXCMG_OK) return e;
+  size_t a = 0, b = 0;
+  for (size_t k = 0; k < items.size(); ++k) items[k] = where[k] ? large[b++] : small[a++];
+  return EXCMG_OK;
+}
+
+excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excmg_options* o,
+                              int nslots, const int* fixed, bool mixed) {
   const int n = (int)items.size();
   std::vector<CGState> hs;
   std::vector<ResDesc> hr;
@@ -722,6 +771,7 @@ void excmg_default_options(excmg_options* o) {
   o->fixed_iters = nullptr;
   o->tile_z = 0;
   o->chunk = 0;
+  o->mixed_min_nodes = 0;
   o->profile = 0;
 }
 
@@ -746,7 +796,7 @@ int excmg_num_levels(const excmg_grid* grid) {
 size_t excmg_workspace_size(const excmg_grid* grid, const excmg_options* opt) {
   const auto lv = levels_of(grid);
   if (lv.empty() || !options_ok(opt)) return 0;
-  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false).bytes;
+  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt)).bytes;
 }
 
 size_t excmg_workspace_size_batched(int nprob, const excmg_grid* grids, const excmg_options* opt) {
@@ -755,7 +805,7 @@ size_t excmg_workspace_size_batched(int nprob, const excmg_grid* grids, const ex
   for (int i = 0; i < nprob; ++i) {
     const auto lv = levels_of(&grids[i]);
     if (lv.empty()) return 0;
-    total += prob_layout(lv, opt->precision == EXCMG_MIXED, false).bytes;
+    total += prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt)).bytes;
   }
   return total;
 }
@@ -785,7 +835,7 @@ excmg_status excmg_solve(const excmg_grid* grid, const double* f, const double* 
   P[0].g = g;
   P[0].u = u;
   P[0].base = c.ws + c.H.bytes;
-  P[0].L = prob_layout(lv, opt->precision == EXCMG_MIXED, false);
+  P[0].L = prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt));
   return run_excmg(P, opt, u_tilde, stats, c);
 }
 
@@ -814,7 +864,7 @@ excmg_status excmg_solve_batched(int nprob, const excmg_grid* grids, const doubl
     P[i].g = g[i];
     P[i].u = u[i];
     P[i].base = base;
-    P[i].L = prob_layout(P[i].lv, opt->precision == EXCMG_MIXED, false);
+    P[i].L = prob_layout(P[i].lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt));
     base += P[i].L.bytes;
   }
   return run_excmg(P, opt, nullptr, stats, c);
@@ -872,7 +922,7 @@ excmg_status excmg_grad(const excmg_grid* grid, const double* u, double* ux, dou
 size_t excmg_workspace_size_level(const excmg_grid* grid, const excmg_options* opt) {
   const auto lv = single_level(grid);
   if (lv.empty() || !options_ok(opt)) return 0;
-  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false).bytes;
+  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt)).bytes;
 }
 
 excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_options* opt,
@@ -893,7 +943,7 @@ excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_optio
   p.g = u;
   p.u = u;
   p.base = c.ws + c.H.bytes;
-  p.L = prob_layout(lv, opt->precision == EXCMG_MIXED, false);
+  p.L = prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt));
   const int l = (int)lv.size() - 1;
   std::vector<Item> items{make_item(p, l, 0, opt)};
   items[0].eps = opt->eps;
@@ -962,7 +1012,7 @@ size_t excmg_workspace_size_adjoint(const excmg_grid* grid, const excmg_options*
   std::vector<Level> lv{{grid->Nx, grid->Ny, grid->Nz}};
   // lambda (float64) + the CG vectors of one level
   return header_layout(1).bytes + align_up(sizeof(double) * nf) +
-         prob_layout(lv, opt->precision == EXCMG_MIXED, false).bytes;
+         prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt)).bytes;
 }
 
 excmg_status excmg_adjoint(const excmg_grid* grid, const double* dLdu, const excmg_options* opt,
@@ -989,7 +1039,7 @@ excmg_status excmg_adjoint(const excmg_grid* grid, const double* dLdu, const exc
   p.g = nullptr;
   p.u = lam;
   p.base = c.ws + c.H.bytes + align_up(sizeof(double) * nf);
-  p.L = prob_layout(p.lv, opt->precision == EXCMG_MIXED, false);
+  p.L = prob_layout(p.lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt));
   c.persistent_ok = (long long)kMaxGrid * (2LL * opt->max_iter + 4) < (1LL << 32);
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
   CK(cudaMemsetAsync(lam, 0, sizeof(double) * nf, c.s));

@@ -19,6 +19,11 @@ constexpr int kThreads = 256;    // threads of every tiled kernel
 constexpr int kTX = 32;          // x-width of a stencil tile (one warp)
 constexpr int kTY = 8;           // y-rows of a stencil tile
 constexpr int kMaxGrid = 4096;   // cap on persistent grid size (partials per problem)
+constexpr int kSmallNodes = 1536;  // grids up to this many nodes: single-block CG
+constexpr int kSmallThreads = 128;
+// MIXED mode solves grids below this many nodes in float64 by default: there CG is
+// latency-bound, float32 saves nothing and refinement would add host round trips.
+constexpr long long kMixedMinNodes = 1LL << 21;
 
 struct Grid3 {
   int nx, ny, nz;      // cells per direction
@@ -134,6 +139,10 @@ int persistent_grid(long long total_tiles);
 // device has no cooperative launch.
 template <typename T>
 int persistent_cg_blocks();
+// All CG steps of ONE problem of at most kSmallNodes nodes in one block, with x, r, p, q
+// in shared memory.
+template <typename T>
+cudaError_t launch_cg_small(const CGDesc<T>* descs, long long nodes, CGState* st, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cg_persistent(const CGDesc<T>* descs, long long total_tiles, int grid,
                                  CGState* st, double* partials, unsigned* bar, int* err,

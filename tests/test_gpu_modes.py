@@ -43,13 +43,14 @@ def test_mixed_error_within_fp64(X, name, N, N0, eps):
     f, g, u = P.make_inputs(P.PROBLEMS[name], N)
     fd, gd = dev(f), dev(g)
     r64 = X.solve(fd, gd, L, N0, eps=eps)
-    rmx = X.solve(fd, gd, L, N0, eps=eps, precision="mixed")
+    rmx = X.solve(fd, gd, L, N0, eps=eps, precision="mixed", mixed_min_nodes=1)
     e64 = np.max(np.abs(host(r64["u"]) - u))
     emx = np.max(np.abs(host(rmx["u"]) - u))
     assert emx <= 1.05 * e64, (emx, e64)
     l2_64 = np.sqrt(np.mean((host(r64["u"]) - u) ** 2))
     l2_mx = np.sqrt(np.mean((host(rmx["u"]) - u) ** 2))
     assert l2_mx <= 1.05 * l2_64
+    assert any(r > 0 for r in rmx["stats"]["refinements"])  # the float32 path ran
     # every level met the tolerance in the float64 residual
     assert all(r <= eps * 1.0000001 for r in rmx["stats"]["relres"][2:])
     assert all(r <= 1e-12 * 1.0000001 for r in rmx["stats"]["relres"][:2])
@@ -59,7 +60,8 @@ def test_mixed_matches_oracle_to_tolerance(X):
     """Both solutions are within the CG tolerance of the discrete solution."""
     N, N0, L = (32, 32, 32), (4, 4, 4), (1.0, 1.0, 1.0)
     f, g, _ = P.make_inputs(P.PROBLEMS["ex3"], N)
-    rmx = X.solve(dev(f), dev(g), L, N0, eps=1e-12, eps_coarse=1e-12, precision="mixed")
+    rmx = X.solve(dev(f), dev(g), L, N0, eps=1e-12, eps_coarse=1e-12, precision="mixed",
+                  mixed_min_nodes=1)
     ref = O.excmg(f, g, L, N, N0, eps=1e-14, eps_coarse=1e-14)
     uo = ref["u"][-1]
     assert np.max(np.abs(host(rmx["u"]) - uo)) / np.max(np.abs(uo)) <= 1e-9
@@ -82,9 +84,10 @@ def test_batched_matches_single_solves(X, precision):
     probs = _batch(20151507, 6, (16, 32, 64))
     eps = 1e-10
     batch = [X.BatchedProblem(L, N, N0, dev(f), dev(g)) for L, N, N0, f, g, _ in probs]
-    res = X.solve_batched(batch, eps=eps, precision=precision)
+    kw = dict(mixed_min_nodes=1) if precision == "mixed" else {}
+    res = X.solve_batched(batch, eps=eps, precision=precision, **kw)
     for (L, N, N0, f, g, u), ub, st in zip(probs, res["u"], res["stats"]):
-        single = X.solve(dev(f), dev(g), L, N0, eps=eps, precision=precision)
+        single = X.solve(dev(f), dev(g), L, N0, eps=eps, precision=precision, **kw)
         a, b = host(ub), host(single["u"])
         # same algorithm, different reduction order: equal to far below the tolerance
         assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b)) + 1e-12
@@ -131,7 +134,8 @@ def test_adjoint_central_differences(X, precision):
         return float(np.sum((u - ut) ** 2)), u
 
     L0, u0 = loss(f, g)
-    df, dg, _ = X.adjoint(dev(2.0 * (u0 - ut)), L, eps=1e-14, precision=precision)
+    kwa = dict(mixed_min_nodes=1) if precision == "mixed" else {}
+    df, dg, _ = X.adjoint(dev(2.0 * (u0 - ut)), L, eps=1e-14, precision=precision, **kwa)
     df, dg = host(df), host(dg)
     delta = 1e-3
     for m in [(8, 8, 8), (3, 12, 5), (1, 1, 1), (0, 7, 9), (15, 2, 16)]:

@@ -56,7 +56,8 @@ def test_invalid_grids_rejected(X, N, N0):
 
 def test_invalid_options_rejected(X):
     g = X.make_grid((1, 1, 1), (32, 32, 32), (4, 4, 4))
-    for kw in ({"precision": 7}, {"eps": -1.0}, {"max_iter": -3}, {"precision": "mixed", "inner_tol": 2.0}):
+    for kw in ({"precision": 7}, {"eps": -1.0}, {"max_iter": -3}, {"precision": "mixed", "inner_tol": 2.0},
+               {"mixed_min_nodes": -1}):
         o, _ = X.make_options(**kw)
         assert X.excmg_workspace_size(ctypes.byref(g), ctypes.byref(o)) == 0
 
