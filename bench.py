@@ -41,12 +41,14 @@ WORKLOADS = {
     "c1": ("sin3", (1.0, 1.0, 1.0), (32, 32, 32), (4, 4, 4), 1e-8, 1e-12),
     "c3": ("r53", (1.0, 1.0, 1.0), (1024, 512, 512), (8, 4, 4), 1e-9, 1e-12),
 }
+PRECISION = {"c1": "fp64", "c2": "fp64", "c3": "mixed"}
 DESCRIPTION = {
     "c2": "FP64 EXCMG, [0,1]^3, 512x256x128 cells (hx=1/512, hy=1/256, hz=1/128), "
           "u=exp(x+y+z), f=3u, g=u; 7 grids from 8x4x2; eps 1e-9 (levels>=2), 1e-12 (two coarsest)",
     "c1": "FP64 EXCMG, [0,1]^3, 32^3 cells, u=sin(pi x)sin(pi y)sin(pi z), f=-3pi^2 u, g=0; "
           "4 grids from 4^3; eps 1e-8 / 1e-12",
-    "c3": "EXCMG, [0,1]^3, 1024x512x512 cells, u=r^(5/3), f=(40/9) r^(-1/3), g=u; "
+    "c3": "MIXED EXCMG (float32 CG inside float64 refinement on grids of >= 2^21 nodes), "
+          "[0,1]^3, 1024x512x512 cells, u=r^(5/3), f=(40/9) r^(-1/3), g=u; "
           "8 grids from 8x4x4; eps 1e-9 / 1e-12",
 }
 
@@ -102,17 +104,18 @@ def source_hash(fname):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def recorded_traffic(kind):
-    """Per-node DRAM bytes of a kernel from a committed ncu summary, if the kernel source
-    is unchanged since (profiles/ncu_traffic.txt: kind bytes_per_node source_sha)."""
+def recorded_traffic(kind, workload):
+    """Per-node DRAM bytes of a kernel on this workload from a committed ncu summary, if
+    the kernel source is unchanged since (profiles/ncu_traffic.txt: kind workload
+    bytes_per_node source_sha)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kind:
-            if parts[2] == source_hash(KERNEL_SOURCE[kind]):
-                return float(parts[1])
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kind and parts[1] == workload:
+            if parts[3] == source_hash(KERNEL_SOURCE[kind]):
+                return float(parts[2])
     return None
 
 
@@ -246,7 +249,8 @@ def main():
     fd = torch.from_numpy(f).to(device)
     gd = torch.from_numpy(g).to(device)
     ud = torch.empty_like(fd)
-    opts = dict(eps=eps, eps_coarse=epsc)
+    prec = PRECISION[args.workload]
+    opts = dict(eps=eps, eps_coarse=epsc, precision=prec)
     ws = X.workspace(X.solve_workspace_bytes(L, N, N0, **opts), device)
     stream = torch.cuda.current_stream()
 
@@ -335,7 +339,7 @@ def main():
     dk = kernels[dom]
     launches_dom = prof[dom]["launches"]
     nodes_per_launch = prof[dom]["nodes"] / launches_dom  # node-steps for persistent CG
-    traffic = recorded_traffic(dom)
+    traffic = recorded_traffic(dom, args.workload)
     if dk["bound"] == "alu":
         roof = {"bound": "alu", "achieved": dk["Gdpop_s"], "peak": DP_PEAK_GOPS,
                 "unit": "G DP-op/s", "frac": dk["Gdpop_s"] / DP_PEAK_GOPS}
@@ -351,14 +355,16 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32+f64",
             "data": "synthetic (closed-form f, g evaluated on the host in float64)",
             "config": {"workload": DESCRIPTION[args.workload], "unknowns": n_unk,
                        "levels": stats["levels"], "iters_per_level": stats["iters"],
                        "relres_finest": stats["relres"][-1],
                        "error_vs_exact": {"L2_rms": err_l2, "Linf": err_linf},
                        "parallelism": f"{world} independent replica(s)",
-                       "l2": "inputs larger than L2 (each finest-level array 136 MB > 129 MB L2)"},
+                       "precision": prec,
+                       "l2": "inputs larger than L2 (each finest-level array >= 136 MB > 129 MB L2)"},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": "unknowns/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / args.steps}}
@@ -367,7 +373,7 @@ def main():
         line.update(extras(X, torch, device, L, N, N0, fd, gd, u_exact, opts, err_l2, err_linf,
                            hbm_peak, args, world))
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "c3":
         secs, ores = oracle_solve_seconds(args.workload, f, g)
         uo = ores["u"][-1]
         line["cpu_baseline"] = {"value": n_unk / secs, "unit": "unknowns/s", "cores": 1,
@@ -473,27 +479,29 @@ def extras(X, torch, device, L, N, N0, fd, gd, u_exact, opts, err_l2, err_linf, 
     out = {}
     n_unk = interior_unknowns(N)
     stream = torch.cuda.current_stream()
-    ws_m = X.workspace(X.solve_workspace_bytes(L, N, N0, precision="mixed", **opts), device)
+    other = "fp64" if opts["precision"] == "mixed" else "mixed"
+    opts = {k: v for k, v in opts.items() if k != "precision"}
+    ws_m = X.workspace(X.solve_workspace_bytes(L, N, N0, precision=other, **opts), device)
     um = torch.empty_like(fd)
     for _ in range(2):
-        X.solve(fd, gd, L, N0, ws=ws_m, out=um, precision="mixed", **opts)
+        X.solve(fd, gd, L, N0, ws=ws_m, out=um, precision=other, **opts)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k = max(3, args.steps // 2)
     a.record(stream)
     for _ in range(k):
-        rm = X.solve(fd, gd, L, N0, ws=ws_m, out=um, precision="mixed", **opts)
+        rm = X.solve(fd, gd, L, N0, ws=ws_m, out=um, precision=other, **opts)
     b.record(stream)
     torch.cuda.synchronize()
     msm = a.elapsed_time(b) / k
     uhm = um.cpu().numpy()
     e2m = float(np.sqrt(np.mean((uhm - u_exact) ** 2)))
     eim = float(np.max(np.abs(uhm - u_exact)))
-    out["mixed"] = {"value": n_unk * world / (msm / 1e3), "ms_per_step": msm,
+    out[other] = {"value": n_unk * world / (msm / 1e3), "ms_per_step": msm,
                     "iters_per_level": rm["stats"]["iters"],
                     "refinements_per_level": rm["stats"]["refinements"],
                     "error_vs_exact": {"L2_rms": e2m, "Linf": eim},
-                    "error_ratio_vs_fp64": {"L2": e2m / err_l2, "Linf": eim / err_linf}}
+                    "error_ratio_vs_headline": {"L2": e2m / err_l2, "Linf": eim / err_linf}}
     # finest-grid CG rates: fixed 20 iterations from the solution, profiled
     rates = {}
     for prec in ("fp64", "mixed"):

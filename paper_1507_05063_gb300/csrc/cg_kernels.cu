@@ -261,11 +261,20 @@ __device__ __forceinline__ T spmv_tile(const CGDesc<T>& d, long long lt, bool fi
   const T exy = (T)d.A.exy, exz = (T)d.A.exz, eyz = (T)d.A.eyz;
   const T bta = first ? T(0) : beta;
   T Pm1 = T(0), Cm1 = T(0), Tm1 = T(0), Tm2 = T(0), tacc = T(0);
-  PlaneLoad<T> nxt;
+  // float32 keeps two planes in flight (it is bound by load latency), float64 one (it is
+  // bound by the FP64 pipe and short of registers)
+  constexpr bool kDeep = sizeof(T) == 4;
+  PlaneLoad<T> nxt, nxt2;
   load_plane(nxt, g, c, c.z0 - 1, first, r, pold);
+  if (kDeep) load_plane(nxt2, g, c, c.z0, first, r, pold);
   for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
     store_plane(nxt, bta, sp[buf]);
-    if (kk < c.z1) load_plane(nxt, g, c, kk + 1, first, r, pold);
+    if (kDeep) {
+      nxt = nxt2;
+      if (kk + 1 < c.z1) load_plane(nxt2, g, c, kk + 2, first, r, pold);
+    } else if (kk < c.z1) {
+      load_plane(nxt, g, c, kk + 1, first, r, pold);
+    }
     __syncthreads();
     const T P = sp[buf][ty + 1][tx + 1];
     const T SX = sp[buf][ty + 1][tx] + sp[buf][ty + 1][tx + 2];
@@ -409,7 +418,7 @@ __global__ void __launch_bounds__(kThreads)
 // second barrier or broadcast is needed.  Barrier waits are bounded: on time-out the
 // kernel records EXCMG_ERR_TIMEOUT and returns.
 // ---------------------------------------------------------------------------------
-constexpr unsigned long long kSpinLimit = 1ull << 24;  // x >= 64 ns: about a second or more
+constexpr unsigned long long kSpinLimit = 1ull << 24;  // polls; > 1 s with the back-off
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -422,8 +431,9 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
+    // release: this block's writes (ordered before it by the block barrier) become
+    // visible before the arrival; the acquire loads below see every other block's
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     int ok = 1;
     unsigned long long spins = 0;
     while (ld_acquire(bar) < target) {
@@ -431,10 +441,9 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* err) {
         ok = 0;
         break;
       }
-      __nanosleep(64);
+      if (spins > 4096) __nanosleep(64);  // tight polling first, back off on long waits
     }
     if (!ok) atomicExch(err, 1);
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -458,16 +467,21 @@ __device__ double sum_partials_all(const double* part, int n) {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
-    k_cg_persistent(const CGDesc<T>* __restrict__ descs, long long total_tiles, CGState* st,
-                    double* partials, unsigned* bar, int* err) {
+    k_cg_persistent(int nprob, const CGDesc<T>* __restrict__ descs, CGState* st,
+                    double* partials, unsigned* bars) {
   __shared__ T sp[2][kTY + 2][kTX + 2];
   __shared__ double s_scalar;
-  const CGDesc<T>& d = descs[0];
+  int p = 0;
+  while (p + 1 < nprob && (int)blockIdx.x >= descs[p + 1].blk_begin) ++p;
+  const CGDesc<T>& d = descs[p];
+  const int G = d.blk_count, bl = (int)blockIdx.x - d.blk_begin;
   CGState* S = st + d.slot;
-  if (S->done) return;  // same value in every block: nothing to do
-  const int G = gridDim.x;
-  double* partA = partials;
-  double* partB = partials + G;
+  if (S->done) return;  // same value in every block of this problem
+  const long long total_tiles = d.t.count();
+  double* partA = partials + (long long)p * 2 * kMaxGrid;
+  double* partB = partA + G;
+  unsigned* bar = bars + 2 * p;
+  int* err = reinterpret_cast<int*>(bars + 2 * p + 1);
   double rr = S->rr, beta = S->beta, tol2 = S->tol2, pq = 0.0, alpha = 0.0;
   int iter = S->iter;
   const int max_iter = S->max_iter, fixed = S->fixed;
@@ -475,16 +489,24 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
   int status = EXCMG_OK;
   unsigned nbar = 0;
   int buf = 0;
+  // a problem with one block needs no grid barrier, only the block's own
+  auto sync_all = [&]() -> bool {
+    if (G == 1) {
+      __syncthreads();
+      return true;
+    }
+    return grid_barrier(bar, ++nbar * (unsigned)G, err);
+  };
   for (;;) {
     // K1 body
     const T* pold = (iter & 1) ? d.pb : d.pa;
     T* pnew = (iter & 1) ? d.pa : d.pb;
     double acc = 0.0;
-    for (long long t = blockIdx.x; t < total_tiles; t += G)
+    for (long long t = bl; t < total_tiles; t += G)
       acc += (double)spmv_tile<T>(d, t, first, (T)beta, pold, pnew, sp, buf);
     double bs = block_sum(acc);
-    if (threadIdx.x == 0) partA[blockIdx.x] = bs;
-    if (!grid_barrier(bar, ++nbar * (unsigned)G, err)) {
+    if (threadIdx.x == 0) partA[bl] = bs;
+    if (!sync_all()) {
       status = EXCMG_ERR_TIMEOUT;
       break;
     }
@@ -500,11 +522,10 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
     alpha = rr / pq;
     // K2 body
     acc = 0.0;
-    for (long long t = blockIdx.x; t < total_tiles; t += G)
-      acc += (double)update_tile<T>(d, t, (T)alpha, pnew);
+    for (long long t = bl; t < total_tiles; t += G) acc += (double)update_tile<T>(d, t, (T)alpha, pnew);
     bs = block_sum(acc);
-    if (threadIdx.x == 0) partB[blockIdx.x] = bs;
-    if (!grid_barrier(bar, ++nbar * (unsigned)G, err)) {
+    if (threadIdx.x == 0) partB[bl] = bs;
+    if (!sync_all()) {
       status = EXCMG_ERR_TIMEOUT;
       break;
     }
@@ -526,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
       break;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bl == 0 && threadIdx.x == 0) {
     S->rr = rr;
     S->pq = pq;
     S->alpha = alpha;
@@ -542,10 +563,11 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
 // K3: r = LHS(u) - RHS(f) = b - A u_I (float64), sums r.r and b.b, CG state init
 // ---------------------------------------------------------------------------------
 template <typename TR>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     k_residual(int nprob, const ResDesc* __restrict__ descs, long long total_tiles,
                CGState* st, double* partials, unsigned* counters) {
   __shared__ double su[2][kTY + 2][kTX + 2];
+  __shared__ double sf[2][kTY + 2][kTX + 2];
   __shared__ int s_active[kMaxProb];
   __shared__ double s_part[2 * kMaxProb];
   for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
@@ -588,18 +610,28 @@ __global__ void __launch_bounds__(kThreads)
     // C/T terms (see k_dir_spmv_dot) of the stencil of u over all 19 nodes, and of its
     // boundary part: b = LHS(boundary part of u) - RHS(f)
     double Cm1 = 0, Tm1 = 0, Tm2 = 0, LCm1 = 0, LTm1 = 0, LTm2 = 0;
+    // right-hand side (6 f_c + 6 face f)/2, split per plane: Fxy_k = 6 f + the 4 in-plane
+    // face values, and the centre values f_{k-1}, f_{k+1} of the neighbouring planes
+    double Fxy_m1 = 0, fc_m1 = 0, fc_m2 = 0;
+    const bool use_f = d.src == nullptr;
     for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
       const bool plane_in = (kk >= 0) && (kk <= g.nz);
       const bool plane_bnd = (kk == 0) || (kk == g.nz);
       for (int idx = threadIdx.x; idx < (kTX + 2) * (kTY + 2); idx += kThreads) {
         const int ly = idx / (kTX + 2), lx = idx - ly * (kTX + 2);
         const int gi = c.x0 - 1 + lx, gj = c.y0 - 1 + ly;
-        double v = 0.0;
-        if (plane_in && gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny)
+        double v = 0.0, fv = 0.0;
+        if (plane_in && gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny) {
           v = u[gi + gj * g.sy + (long long)kk * g.sz];
+          if (use_f) fv = d.f.at(gi, gj, kk);
+        }
         su[buf][ly][lx] = v;
+        sf[buf][ly][lx] = fv;
       }
       __syncthreads();
+      const double fc = sf[buf][ty + 1][tx + 1];
+      const double Fxy = fma(6.0, fc, (sf[buf][ty + 1][tx] + sf[buf][ty + 1][tx + 2]) +
+                                          (sf[buf][ty][tx + 1] + sf[buf][ty + 2][tx + 1]));
       const double P = su[buf][ty + 1][tx + 1];
       const double W = su[buf][ty + 1][tx], E = su[buf][ty + 1][tx + 2];
       const double S = su[buf][ty][tx + 1], N = su[buf][ty + 2][tx + 1];
@@ -628,12 +660,7 @@ __global__ void __launch_bounds__(kThreads)
         const bool interior = inxy && kc > 0 && kc < g.nz;
         double rv = 0.0;
         if (interior) {
-          const View& F = d.f;
-          const double rhs =
-              d.src ? -d.src[o]
-                    : 0.5 * (6.0 * F.at(i, j, kc) + ((F.at(i - 1, j, kc) + F.at(i + 1, j, kc)) +
-                                                     (F.at(i, j - 1, kc) + F.at(i, j + 1, kc)) +
-                                                     (F.at(i, j, kc - 1) + F.at(i, j, kc + 1))));
+          const double rhs = use_f ? 0.5 * (Fxy_m1 + (fc_m2 + fc)) : -d.src[o];
           // LHS(u) = -(A-stencil of u over all 19 nodes)
           rv = -((Cm1 + Tm2) + Tk) - rhs;
           acc_r = fma(rv, rv, acc_r);
@@ -650,6 +677,9 @@ __global__ void __launch_bounds__(kThreads)
       LTm2 = LTm1;
       LTm1 = LTk;
       LCm1 = LCk;
+      fc_m2 = fc_m1;
+      fc_m1 = fc;
+      Fxy_m1 = Fxy;
       buf ^= 1;
     }
   }
@@ -865,18 +895,16 @@ template cudaError_t launch_cg_small<double>(const CGDesc<double>*, long long, C
 template cudaError_t launch_cg_small<float>(const CGDesc<float>*, long long, CGState*, cudaStream_t);
 
 template <typename T>
-cudaError_t launch_cg_persistent(const CGDesc<T>* descs, long long total_tiles, int grid,
-                                 CGState* st, double* partials, unsigned* bar, int* err,
-                                 cudaStream_t s) {
-  void* args[] = {(void*)&descs, (void*)&total_tiles, (void*)&st, (void*)&partials, (void*)&bar,
-                  (void*)&err};
+cudaError_t launch_cg_persistent(int nprob, const CGDesc<T>* descs, int grid, CGState* st,
+                                 double* partials, unsigned* bar, cudaStream_t s) {
+  void* args[] = {(void*)&nprob, (void*)&descs, (void*)&st, (void*)&partials, (void*)&bar};
   return cudaLaunchCooperativeKernel((const void*)k_cg_persistent<T>, dim3(grid), dim3(kThreads),
                                      args, 0, s);
 }
-template cudaError_t launch_cg_persistent<double>(const CGDesc<double>*, long long, int, CGState*,
-                                                  double*, unsigned*, int*, cudaStream_t);
-template cudaError_t launch_cg_persistent<float>(const CGDesc<float>*, long long, int, CGState*,
-                                                 double*, unsigned*, int*, cudaStream_t);
+template cudaError_t launch_cg_persistent<double>(int, const CGDesc<double>*, int, CGState*, double*,
+                                                  unsigned*, cudaStream_t);
+template cudaError_t launch_cg_persistent<float>(int, const CGDesc<float>*, int, CGState*, double*,
+                                                 unsigned*, cudaStream_t);
 
 int persistent_grid(long long total_tiles) {
   if (g_max_grid == 0) {

@@ -182,8 +182,9 @@ struct Header {
   size_t bytes;
 };
 
-// States: one per problem of a batch, or one per level of a single solve.
-int state_slots(int nprob) { return std::max(nprob, (int)EXCMG_MAX_LEVELS); }
+// States: one per (problem, level): slot = problem * EXCMG_MAX_LEVELS + level.
+int state_slots(int nprob) { return std::max(nprob, 1) * (int)EXCMG_MAX_LEVELS; }
+int slot_of(int problem, int level) { return problem * (int)EXCMG_MAX_LEVELS + level; }
 
 Header header_layout(int nprob) {
   Header H;
@@ -192,8 +193,8 @@ Header header_layout(int nprob) {
   off = align_up(off + sizeof(CGState) * state_slots(nprob));
   H.counters = off;
   off = align_up(off + sizeof(unsigned) * state_slots(nprob));
-  H.bar = off;  // grid-barrier arrival count (unsigned) + time-out flag (int)
-  off = align_up(off + 2 * sizeof(unsigned));
+  H.bar = off;  // per problem: grid-barrier arrival count (unsigned) + time-out flag (int)
+  off = align_up(off + 2 * sizeof(unsigned) * std::max(nprob, 1));
   H.partials = off;
   off = align_up(off + sizeof(double) * 2 * (size_t)nprob * kMaxGrid);
   H.cgd = off;
@@ -322,45 +323,69 @@ excmg_status read_states(const Ctx& c, int nprob, std::vector<CGState>& hs) {
 // Runs CG steps over the problems described by `descs` (device copy, `n` entries) until
 // every one of them is done.  Returns the number of convergence reads.
 template <typename T>
-excmg_status cg_loop(const Ctx& c, int n, const CGDesc<T>* ddesc, long long tiles, int grid,
+excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int grid,
                      const std::vector<int>& slots, int nslots, int chunk0,
-                     std::vector<CGState>& hs, double nodes) {
-  // A single problem runs all its steps in one cooperative launch when the device
-  // supports it and the barrier count cannot wrap.
-  if (n == 1) {
-    const int coop = persistent_cg_blocks<T>();
-    if (coop > 0 && c.persistent_ok) {
-      const int g = (int)std::min<long long>(tiles, coop);
-      const bool small = nodes <= (double)kSmallNodes;
-      auto launch = [&]() -> cudaError_t {
-        if (small) return launch_cg_small<T>(ddesc, (long long)nodes, c.st(), c.s);
-        cudaError_t e = cudaMemsetAsync(c.bar(), 0, 2 * sizeof(unsigned), c.s);
-        if (e != cudaSuccess) return e;
-        return launch_cg_persistent<T>(ddesc, tiles, g, c.st(), c.partials(), c.bar(), c.bar_err(), c.s);
-      };
-      const int kind = small ? (sizeof(T) == 8 ? EXCMG_K_CG_SMALL_F64 : EXCMG_K_CG_SMALL_F32)
-                             : (sizeof(T) == 8 ? EXCMG_K_CG_F64 : EXCMG_K_CG_F32);
-      if (c.launches) *c.launches += 1;
-      if (c.prof) {
-        const size_t a = c.prof->event(), b = c.prof->event();
-        if (c.prof->pool[a]) cudaEventRecord(c.prof->pool[a], c.s);
-        CK(launch());
-        if (c.prof->pool[b]) cudaEventRecord(c.prof->pool[b], c.s);
-        c.prof->recs.push_back({kind, a, b, nodes, true, slots[0]});
-      } else {
-        CK(launch());
+                     std::vector<CGState>& hs, double nodes, std::vector<CGDesc<T>>& hd) {
+  // Every problem runs all its CG steps inside one cooperative launch when the device
+  // supports it (and the barrier count cannot wrap): problem p gets a block range
+  // proportional to its tiles and iterates on its own.  A single small grid runs in one
+  // block with its vectors in shared memory.
+  const int coop = persistent_cg_blocks<T>();
+  if (coop >= n && coop > 0 && c.persistent_ok) {
+    const bool small = n == 1 && nodes <= (double)kSmallNodes;
+    int grid_total = 0;
+    if (!small) {
+      long long wsum = 0;
+      for (int p = 0; p < n; ++p) wsum += hd[p].t.count();
+      std::vector<int> g(n);
+      int gsum = 0;
+      for (int p = 0; p < n; ++p) {
+        const long long tp = hd[p].t.count();
+        long long v = (long long)((double)coop * (double)tp / (double)std::max(wsum, 1LL));
+        v = std::max(1LL, std::min(v, tp));
+        g[p] = (int)v;
+        gsum += g[p];
       }
-      if (c.defer) return EXCMG_OK;
-      excmg_status e = read_states(c, nslots, hs);
-      if (e == EXCMG_OK && c.prof) {
-        // states are read now: count the steps before a later residual resets them
-        Prof::Rec& rec = c.prof->recs.back();
-        rec.nodes *= hs[slots[0]].iter;
-        rec.iter_slot = -1;
-        rec.real = hs[slots[0]].iter > 0;
+      while (gsum > coop) {  // give back blocks from the largest shares
+        int q = (int)(std::max_element(g.begin(), g.end()) - g.begin());
+        if (g[q] <= 1) break;
+        --g[q];
+        --gsum;
       }
-      return e;
+      for (int p = 0; p < n; ++p) {
+        hd[p].blk_begin = grid_total;
+        hd[p].blk_count = g[p];
+        grid_total += g[p];
+      }
+      CK(cudaMemcpyAsync(ddesc, hd.data(), sizeof(CGDesc<T>) * n, cudaMemcpyHostToDevice, c.s));
+      CK(cudaMemsetAsync(c.bar(), 0, 2 * sizeof(unsigned) * n, c.s));
     }
+    auto launch = [&]() -> cudaError_t {
+      if (small) return launch_cg_small<T>(ddesc, (long long)nodes, c.st(), c.s);
+      return launch_cg_persistent<T>(n, ddesc, grid_total, c.st(), c.partials(), c.bar(), c.s);
+    };
+    const int kind = small ? (sizeof(T) == 8 ? EXCMG_K_CG_SMALL_F64 : EXCMG_K_CG_SMALL_F32)
+                           : (sizeof(T) == 8 ? EXCMG_K_CG_F64 : EXCMG_K_CG_F32);
+    if (c.launches) *c.launches += 1;
+    if (c.prof && n == 1) {
+      const size_t a = c.prof->event(), b = c.prof->event();
+      if (c.prof->pool[a]) cudaEventRecord(c.prof->pool[a], c.s);
+      CK(launch());
+      if (c.prof->pool[b]) cudaEventRecord(c.prof->pool[b], c.s);
+      c.prof->recs.push_back({kind, a, b, nodes, true, slots[0]});
+    } else {
+      CK(launch());
+    }
+    if (c.defer) return EXCMG_OK;
+    excmg_status e = read_states(c, nslots, hs);
+    if (e == EXCMG_OK && c.prof && n == 1) {
+      // states are read now: count the steps before a later residual resets them
+      Prof::Rec& rec = c.prof->recs.back();
+      rec.nodes *= hs[slots[0]].iter;
+      rec.iter_slot = -1;
+      rec.real = hs[slots[0]].iter > 0;
+    }
+    return e;
   }
   int chunk = chunk0 > 0 ? chunk0 : 4;
   Prof* prof = (c.prof && n == 1) ? c.prof : nullptr;
@@ -475,7 +500,10 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     tiles += r.t.count();
     if (mixed) {
       r.r = it.d32.r;
-      r.tol_b2 = 0.0;
+      // the inner solve stops at inner_tol x its starting residual, or as soon as its
+      // residual is below half the outer target (more float32 steps would be wasted:
+      // EXCMG's initial guess is often within a few orders of the tolerance)
+      r.tol_b2 = 0.25 * it.eps * it.eps;
       r.tol_r2 = o->inner_tol * o->inner_tol;
       r.fixed = 0;
       r.max_iter = o->max_iter;
@@ -505,7 +533,7 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     CK(c.timed(EXCMG_K_RESIDUAL, nodes_sum, [&] {
       return launch_residual(false, n, c.resd(), tiles, grid, c.st(), c.partials(), c.counters(), c.s);
     }));
-    excmg_status e = cg_loop<double>(c, n, c.cgd(), tiles, grid, slots, nslots, o->chunk, hs, nodes_sum);
+    excmg_status e = cg_loop<double>(c, n, c.cgd(), tiles, grid, slots, nslots, o->chunk, hs, nodes_sum, hd);
     if (e != EXCMG_OK) return e;
     if (c.defer) return EXCMG_OK;  // the caller reads every state at the end
     for (auto& it : items) {
@@ -574,7 +602,7 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     for (int a : next) fnodes += (double)items[a].nodes;
     CK(cudaMemcpyAsync(c.cgf(), fd.data(), sizeof(CGDesc<float>) * nf, cudaMemcpyHostToDevice, c.s));
     CK(c.timed(EXCMG_K_CORRECT, fnodes, [&] { return launch_scale_rhs(nf, c.cgf(), ft, fgrid, c.st(), c.s); }));
-    e = cg_loop<float>(c, nf, c.cgf(), ft, fgrid, fslots, nslots, o->chunk, hs, fnodes);
+    e = cg_loop<float>(c, nf, c.cgf(), ft, fgrid, fslots, nslots, o->chunk, hs, fnodes, fd);
     if (e != EXCMG_OK) return e;
     for (int a : next) {
       items[a].iters += hs[items[a].d32.slot].iter;
@@ -632,13 +660,12 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
   c.launches = &launches;
   Prof prof;
   if (o->profile && np == 1) c.prof = &prof;
-  // a single solve keeps one CG state per level and reads them all at the end
-  const bool single = np == 1;
+  // one CG state per (problem, level); an FP64 solve reads them all once, at the end
   long long max_count = o->max_iter;
   if (o->fixed_iters)
     for (size_t l = 0; l < P[0].lv.size(); ++l) max_count = std::max<long long>(max_count, o->fixed_iters[l]);
-  c.persistent_ok = single && (long long)kMaxGrid * (2 * max_count + 4) < (1LL << 32);
-  c.defer = single && o->precision == EXCMG_FP64;
+  c.persistent_ok = (long long)kMaxGrid * (2 * max_count + 4) < (1LL << 32);
+  c.defer = o->precision == EXCMG_FP64;
   struct Report {
     excmg_stats* st;
     long long* n;
@@ -706,11 +733,10 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
     std::vector<Item> items;
     std::vector<int> fixed;
     for (int a = 0; a < na; ++a) {
-      items.push_back(make_item(P[act[a]], lev[a], single ? lev[a] : act[a], o));
+      items.push_back(make_item(P[act[a]], lev[a], slot_of(act[a], lev[a]), o));
       if (o->fixed_iters) fixed.push_back(o->fixed_iters[lev[a]]);
     }
-    excmg_status e = solve_items(c, items, o, single ? state_slots(1) : np,
-                                 o->fixed_iters ? fixed.data() : nullptr);
+    excmg_status e = solve_items(c, items, o, state_slots(np), o->fixed_iters ? fixed.data() : nullptr);
     if (e != EXCMG_OK) return e;
     if (c.defer) continue;
     for (int a = 0; a < na; ++a) {
@@ -739,15 +765,16 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
     if (e != EXCMG_OK) return e;
   }
   if (c.defer) {
-    for (int l = 0; l < (int)P[0].lv.size(); ++l) {
-      const CGState& S = hs[l];
-      if (stats) {
-        stats[0].iters[l] = S.iter;
-        stats[0].relres[l] = S.bb > 0 ? sqrt(S.rr / S.bb) : 0.0;
+    for (int i = 0; i < np; ++i)
+      for (int l = 0; l < (int)P[i].lv.size(); ++l) {
+        const CGState& S = hs[slot_of(i, l)];
+        if (stats) {
+          stats[i].iters[l] = S.iter;
+          stats[i].relres[l] = S.bb > 0 ? sqrt(S.rr / S.bb) : 0.0;
+        }
+        if (S.status != EXCMG_OK && (result == EXCMG_OK || S.status == EXCMG_ERR_NONFINITE))
+          result = (excmg_status)S.status;
       }
-      if (S.status != EXCMG_OK && (result == EXCMG_OK || S.status == EXCMG_ERR_NONFINITE))
-        result = (excmg_status)S.status;
-    }
   }
   if (c.prof) prof.report(stats, hs);
   return result;

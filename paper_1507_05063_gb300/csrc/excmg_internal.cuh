@@ -91,6 +91,8 @@ struct CGDesc {
   double* aux;            // MIXED inner solve: the float64 level solution u += x / scale
   double scale;           // MIXED inner solve: it solves A x = scale * r (r scaled to O(1)
                           // so float32 products neither underflow nor overflow)
+  int blk_begin;          // persistent CG: this problem's blocks are [blk_begin,
+  int blk_count;          //   blk_begin + blk_count) of the cooperative grid
 };
 
 // One problem of a residual phase: r = LHS(u) - RHS(f) (= b - A u_I) in float64,
@@ -132,11 +134,13 @@ cudaError_t launch_scale_rhs(int nprob, const CGDesc<float>* inner, long long to
                              int grid, CGState* st, cudaStream_t s);
 int persistent_grid(long long total_tiles);
 
-// All CG steps of ONE problem in one cooperative launch (grid barriers with bounded
-// waits; EXCMG_ERR_TIMEOUT in the state if a wait runs out).  `bar` (zeroed before the
-// launch) counts barrier arrivals, `err` (zeroed) flags a time-out; `partials` needs 2 x
-// grid doubles.  persistent_cg_blocks() is the largest co-resident grid, or -1 if the
-// device has no cooperative launch.
+// All CG steps of every problem of `descs` in one cooperative launch.  Problem p owns
+// the blocks [blk_begin, blk_begin + blk_count) and iterates independently of the
+// others; its reductions cross a barrier over its own blocks only (bounded waits;
+// EXCMG_ERR_TIMEOUT in its state if a wait runs out).  `bar` holds two zeroed words per
+// problem (arrival count, time-out flag); `partials` 2 x kMaxGrid doubles per problem.
+// persistent_cg_blocks() is the largest co-resident grid, or -1 if the device has no
+// cooperative launch.
 template <typename T>
 int persistent_cg_blocks();
 // All CG steps of ONE problem of at most kSmallNodes nodes in one block, with x, r, p, q
@@ -144,9 +148,8 @@ int persistent_cg_blocks();
 template <typename T>
 cudaError_t launch_cg_small(const CGDesc<T>* descs, long long nodes, CGState* st, cudaStream_t s);
 template <typename T>
-cudaError_t launch_cg_persistent(const CGDesc<T>* descs, long long total_tiles, int grid,
-                                 CGState* st, double* partials, unsigned* bar, int* err,
-                                 cudaStream_t s);
+cudaError_t launch_cg_persistent(int nprob, const CGDesc<T>* descs, int grid, CGState* st,
+                                 double* partials, unsigned* bar, cudaStream_t s);
 
 // Transfer kernels (transfer_kernels.cu).
 struct ProlongDesc {

@@ -87,8 +87,9 @@ __device__ void exp_finite_brick(const ProlongDesc& d, long long lb, BrickSmem& 
       for (int a = 0; a <= oz; ++a)
         for (int bb = 0; bb <= oy; ++bb)
           for (int c = 0; c <= ox; ++c) sum += s_d[cz + a][cy + bb][cx + c];
-      const int ncorner = 1 << (ox + oy + oz);
-      s_w[kz][jy][ix] = s_u1[kz][jy][ix] + sum / (16.0 * ncorner);
+      // (1/16) * mean over 2^(ox+oy+oz) corners: a power-of-two scale, exact as a product
+      const double scale = 0.0625 / (double)(1 << (ox + oy + oz));
+      s_w[kz][jy][ix] = fma(sum, scale, s_u1[kz][jy][ix]);
     }
     __syncthreads();
     // 3a. quartic along x
@@ -183,8 +184,11 @@ __global__ void __launch_bounds__(kThreads)
           const int I = cx + c, J = cy + b, K = cz + a;
           sum += uh[2 * I + 2 * J * g.sy + 2LL * K * g.sz] - u2h[I + J * s1y + K * s1z];
         }
-    const int ncorner = 1 << (ox + oy + oz);
-    ut[o] = uh[o] + sum / (15.0 * ncorner);
+    // (1/15) * mean over the corners; the reciprocals are compile-time constants
+    const double inv = (ox + oy + oz == 0) ? 1.0 / 15.0
+                     : (ox + oy + oz == 1) ? 1.0 / 30.0
+                     : (ox + oy + oz == 2) ? 1.0 / 60.0 : 1.0 / 120.0;
+    ut[o] = fma(sum, inv, uh[o]);
   }
 }
 

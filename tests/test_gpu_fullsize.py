@@ -78,7 +78,11 @@ def test_1024x512x512_mixed_properties(X, c3):
         win_u = uh[k - 1:k + 2, j - 1:j + 2, i - 1:i + 2]
         win_f = f[k - 1:k + 2, j - 1:j + 2, i - 1:i + 2]
         want = O.residual(win_u, win_f, h)[0, 0, 0]
-        scale = np.max(np.abs(O.lhs(np.abs(win_u), h))) + np.max(np.abs(O.rhs(np.abs(win_f))))
+        # rounding scale: sum of |weight| x |value| over the 19 + 7 terms
+        w = O.coefficients(*h)
+        wsum = (abs(w["centre"]) + 2 * (abs(w["fx"]) + abs(w["fy"]) + abs(w["fz"]))
+                + 4 * (abs(w["exy"]) + abs(w["exz"]) + abs(w["eyz"])))
+        scale = wsum * np.max(np.abs(win_u)) + 6.0 * np.max(np.abs(win_f))
         assert abs(rh[k, j, i] - want) <= 1e-13 * scale
 
 
