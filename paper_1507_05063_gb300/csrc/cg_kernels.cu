@@ -418,7 +418,9 @@ __global__ void __launch_bounds__(kThreads)
 // second barrier or broadcast is needed.  Barrier waits are bounded: on time-out the
 // kernel records EXCMG_ERR_TIMEOUT and returns.
 // ---------------------------------------------------------------------------------
-constexpr unsigned long long kSpinLimit = 1ull << 24;  // polls; > 1 s with the back-off
+// polls before a barrier wait gives up: several seconds with the back-off (a team's first
+// barrier may wait for members still finishing another problem)
+constexpr unsigned long long kSpinLimit = 1ull << 25;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -465,18 +467,14 @@ __device__ double sum_partials_all(const double* part, int n) {
 #define EXCMG_PERSIST_MIN_BLOCKS 3
 #endif
 
+// The CG loop of one problem, run by the G = d.blk_count blocks of its team (this block
+// is member bl).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
-    k_cg_persistent(int nprob, const CGDesc<T>* __restrict__ descs, CGState* st,
-                    double* partials, unsigned* bars) {
-  __shared__ T sp[2][kTY + 2][kTX + 2];
-  __shared__ double s_scalar;
-  int p = 0;
-  while (p + 1 < nprob && (int)blockIdx.x >= descs[p + 1].blk_begin) ++p;
-  const CGDesc<T>& d = descs[p];
-  const int G = d.blk_count, bl = (int)blockIdx.x - d.blk_begin;
+__device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* partials,
+                        unsigned* bars, T (*sp)[kTY + 2][kTX + 2], double& s_scalar, int& buf) {
+  const int G = d.blk_count;
   CGState* S = st + d.slot;
-  if (S->done) return;  // same value in every block of this problem
+  if (S->done) return;  // same value in every block of this team
   const long long total_tiles = d.t.count();
   double* partA = partials + (long long)p * 2 * kMaxGrid;
   double* partB = partA + G;
@@ -488,8 +486,7 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
   bool first = S->first != 0;
   int status = EXCMG_OK;
   unsigned nbar = 0;
-  int buf = 0;
-  // a problem with one block needs no grid barrier, only the block's own
+  // a team of one block needs no grid barrier, only the block's own
   auto sync_all = [&]() -> bool {
     if (G == 1) {
       __syncthreads();
@@ -558,6 +555,37 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
     S->done = 1;
   }
 }
+
+// Blocks form one team per problem: each block takes the next slot from an atomic
+// counter; slots [blk_begin, blk_begin + blk_count) of problem p are its team.  Slots
+// are handed out in order, so at most one team is ever partly formed and every earlier
+// team finishes and frees its blocks: a team whose members arrive late only waits.
+// A block whose team is done takes the next slot; a block past the last slot exits.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
+    k_cg_persistent(int nprob, const CGDesc<T>* __restrict__ descs, CGState* st,
+                    double* partials, unsigned* bars) {
+  __shared__ T sp[2][kTY + 2][kTX + 2];
+  __shared__ double s_scalar;
+  __shared__ int s_slot;
+  unsigned* slot_counter = bars + 2 * nprob;
+  int total_slots = 0;
+  for (int q = 0; q < nprob; ++q) total_slots = max(total_slots, descs[q].blk_begin + descs[q].blk_count);
+  int buf = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_slot = (int)atomicAdd(slot_counter, 1u);
+    __syncthreads();
+    const int slot = s_slot;
+    if (slot >= total_slots) return;
+    int p = 0;
+    while (p < nprob && !(slot >= descs[p].blk_begin && slot < descs[p].blk_begin + descs[p].blk_count)) ++p;
+    if (p >= nprob) return;  // unreachable: every slot below total_slots has a team
+    cg_team<T>(descs[p], p, slot - descs[p].blk_begin, st, partials, bars, sp, s_scalar, buf);
+  }
+}
+
+
 
 // ---------------------------------------------------------------------------------
 // K3: r = LHS(u) - RHS(f) = b - A u_I (float64), sums r.r and b.b, CG state init

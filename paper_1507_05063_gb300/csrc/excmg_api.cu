@@ -193,8 +193,8 @@ Header header_layout(int nprob) {
   off = align_up(off + sizeof(CGState) * state_slots(nprob));
   H.counters = off;
   off = align_up(off + sizeof(unsigned) * state_slots(nprob));
-  H.bar = off;  // per problem: grid-barrier arrival count (unsigned) + time-out flag (int)
-  off = align_up(off + 2 * sizeof(unsigned) * std::max(nprob, 1));
+  H.bar = off;  // per problem: barrier arrival count + time-out flag; then the team-slot counter
+  off = align_up(off + (2 * sizeof(unsigned)) * std::max(nprob, 1) + sizeof(unsigned));
   H.partials = off;
   off = align_up(off + sizeof(double) * 2 * (size_t)nprob * kMaxGrid);
   H.cgd = off;
@@ -335,30 +335,28 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
     const bool small = n == 1 && nodes <= (double)kSmallNodes;
     int grid_total = 0;
     if (!small) {
-      long long wsum = 0;
-      for (int p = 0; p < n; ++p) wsum += hd[p].t.count();
-      std::vector<int> g(n);
-      int gsum = 0;
+      // team sizes: a lone problem takes every co-resident block it can use; in a batch
+      // each problem takes about one block per two tiles, and teams are formed in order
+      // of decreasing size (slots are taken in order by the blocks of one launch)
+      std::vector<int> g(n), order(n);
+      long long slots = 0;
       for (int p = 0; p < n; ++p) {
         const long long tp = hd[p].t.count();
-        long long v = (long long)((double)coop * (double)tp / (double)std::max(wsum, 1LL));
-        v = std::max(1LL, std::min(v, tp));
-        g[p] = (int)v;
-        gsum += g[p];
+        const long long want = (n == 1) ? tp : (tp + 1) / 2;
+        g[p] = (int)std::max(1LL, std::min<long long>(want, coop));
+        order[p] = p;
+        slots += g[p];
       }
-      while (gsum > coop) {  // give back blocks from the largest shares
-        int q = (int)(std::max_element(g.begin(), g.end()) - g.begin());
-        if (g[q] <= 1) break;
-        --g[q];
-        --gsum;
-      }
-      for (int p = 0; p < n; ++p) {
-        hd[p].blk_begin = grid_total;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return g[a] > g[b]; });
+      int begin = 0;
+      for (int p : order) {
+        hd[p].blk_begin = begin;
         hd[p].blk_count = g[p];
-        grid_total += g[p];
+        begin += g[p];
       }
+      grid_total = (int)std::min<long long>(slots, coop);
       CK(cudaMemcpyAsync(ddesc, hd.data(), sizeof(CGDesc<T>) * n, cudaMemcpyHostToDevice, c.s));
-      CK(cudaMemsetAsync(c.bar(), 0, 2 * sizeof(unsigned) * n, c.s));
+      CK(cudaMemsetAsync(c.bar(), 0, (2 * sizeof(unsigned)) * n + sizeof(unsigned), c.s));
     }
     auto launch = [&]() -> cudaError_t {
       if (small) return launch_cg_small<T>(ddesc, (long long)nodes, c.st(), c.s);
