@@ -17,6 +17,7 @@
 // Reductions are deterministic: fixed tile order per block, a fixed-order tree per
 // block, and a fixed-order sum of the per-block partials by the last block to arrive.
 #include <math.h>
+#include <stdint.h>
 
 #include <algorithm>
 
@@ -327,6 +328,78 @@ __device__ __forceinline__ T update_tile(const CGDesc<T>& d, long long lt, T alp
   return tacc;
 }
 
+// The update x += alpha p, r -= alpha q over a flat range of a problem's node array
+// (it is elementwise: any partition works once p and q are complete), with 16-byte
+// vector accesses when all four arrays allow them.  Block bl of G takes the chunks
+// bl, bl + G, ... of kChunk elements.  Returns this thread's share of r.r.
+constexpr int kChunk = 4 * kThreads * 2;  // elements per chunk: 2 vector steps per thread
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+__device__ __forceinline__ float4 ldv4(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldv4(const double2* p) { return __ldcg(p); }
+
+template <typename T>
+__device__ __forceinline__ double update_flat(const CGDesc<T>& d, int bl, int G, T alpha,
+                                              const T* __restrict__ pn) {
+  const long long n = d.g.nodes();
+  T* __restrict__ x = d.x;
+  T* __restrict__ r = d.r;
+  const T* __restrict__ q = d.q;
+  double acc = 0.0;
+  constexpr int V = Vec<T>::n;
+  using VT = typename Vec<T>::type;
+  const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
+                     reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(pn)) & 15) == 0;
+  for (long long c0 = (long long)bl * kChunk; c0 < n; c0 += (long long)G * kChunk) {
+    const long long c1 = c0 + kChunk < n ? c0 + kChunk : n;
+    T tacc = T(0);
+    if (vec && c1 - c0 == kChunk) {
+#pragma unroll
+      for (int k = 0; k < kChunk / (V * kThreads); ++k) {
+        const long long o = c0 + ((long long)k * kThreads + threadIdx.x) * V;
+        const VT pv = ldv4(reinterpret_cast<const VT*>(pn + o));
+        const VT qv = ldv4(reinterpret_cast<const VT*>(q + o));
+        VT xv = ldv4(reinterpret_cast<const VT*>(x + o));
+        VT rv = ldv4(reinterpret_cast<const VT*>(r + o));
+        const T* pe = reinterpret_cast<const T*>(&pv);
+        const T* qe = reinterpret_cast<const T*>(&qv);
+        T* xe = reinterpret_cast<T*>(&xv);
+        T* re = reinterpret_cast<T*>(&rv);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          xe[e] = fmaT(alpha, pe[e], xe[e]);
+          re[e] = fmaT(-alpha, qe[e], re[e]);
+          tacc = fmaT(re[e], re[e], tacc);
+        }
+        *reinterpret_cast<VT*>(x + o) = xv;
+        *reinterpret_cast<VT*>(r + o) = rv;
+      }
+    } else {
+      for (long long o = c0 + threadIdx.x; o < c1; o += kThreads) {
+        const T xv = fmaT(alpha, ldv(pn + o), ldv(x + o));
+        const T rv = fmaT(-alpha, ldv(q + o), ldv(r + o));
+        x[o] = xv;
+        r[o] = rv;
+        tacc = fmaT(rv, rv, tacc);
+      }
+    }
+    acc += (double)tacc;
+  }
+  return acc;
+}
+
 // ---------------------------------------------------------------------------------
 // K1: p_new = r + beta p_old, q = A p_new, sum p.q
 // ---------------------------------------------------------------------------------
@@ -517,9 +590,8 @@ __device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* 
       break;
     }
     alpha = rr / pq;
-    // K2 body
-    acc = 0.0;
-    for (long long t = bl; t < total_tiles; t += G) acc += (double)update_tile<T>(d, t, (T)alpha, pnew);
+    // K2 body (elementwise: a flat, vectorised partition of the node array)
+    acc = update_flat<T>(d, bl, G, (T)alpha, pnew);
     bs = block_sum(acc);
     if (threadIdx.x == 0) partB[bl] = bs;
     if (!sync_all()) {
@@ -689,6 +761,7 @@ __global__ void __launch_bounds__(kThreads, 3)
         double rv = 0.0;
         if (interior) {
           const double rhs = use_f ? 0.5 * (Fxy_m1 + (fc_m2 + fc)) : -d.src[o];
+          if (d.rhs_out) d.rhs_out[o] = -rhs;
           // LHS(u) = -(A-stencil of u over all 19 nodes)
           rv = -((Cm1 + Tm2) + Tk) - rhs;
           acc_r = fma(rv, rv, acc_r);

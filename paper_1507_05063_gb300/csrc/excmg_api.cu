@@ -129,6 +129,7 @@ struct ProbLayout {
   size_t coarse_off[EXCMG_MAX_LEVELS];  // u of levels 0 .. L-2 (float64)
   size_t r, pa, pb, q;                  // float64 CG vectors (finest size)
   size_t r32, pa32, pb32, q32, e32;     // float32 CG vectors (MIXED)
+  size_t rhs64;                         // MIXED: -RHS(f) of the level being refined
   size_t bytes;
 };
 
@@ -171,6 +172,8 @@ ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_
     off = align_up(off + sizeof(float) * nf);
     L.e32 = off;
     off = align_up(off + sizeof(float) * nf);
+    L.rhs64 = off;
+    off = align_up(off + sizeof(double) * nf);
   }
   L.bytes = off;
   return L;
@@ -429,6 +432,7 @@ struct Item {
   ResDesc res;
   CGDesc<double> d64;
   CGDesc<float> d32;
+  double* rhs_cache;    // MIXED: -RHS(f) kept between refinement residuals (NULL: none)
   double eps;           // stop at ||r|| <= eps ||b||
   long long nodes;
   // results
@@ -546,13 +550,21 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     CK(cudaMemsetAsync(it.d32.x, 0, sizeof(float) * it.nodes, c.s));
   std::vector<int> cur(n);
   for (int a = 0; a < n; ++a) cur[a] = a;
-  for (;;) {
+  for (int pass = 0;; ++pass) {
     std::vector<ResDesc> rr;
     long long rt = 0;
     for (int a : cur) {
       ResDesc r = items[a].res;
       r.tile_begin = rt;
       rt += r.t.count();
+      if (items[a].rhs_cache && !r.src) {
+        if (pass == 0) {
+          r.rhs_out = items[a].rhs_cache;  // keep -RHS(f) for the later passes
+        } else {
+          r.src = items[a].rhs_cache;      // r = LHS(u) - RHS(f) without recomputing RHS
+          r.want_b = 0;                    // ||b|| is already in the state
+        }
+      }
       rr.push_back(r);
     }
     const int nr = (int)rr.size();
@@ -644,6 +656,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   f.q = reinterpret_cast<float*>(p.base + p.L.q32);
   f.aux = p.level_u(l);
   f.scale = 1.0;
+  it.rhs_cache = p.L.rhs64 ? reinterpret_cast<double*>(p.base + p.L.rhs64) : nullptr;
   return it;
 }
 

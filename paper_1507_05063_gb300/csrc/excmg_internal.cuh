@@ -106,7 +106,9 @@ struct ResDesc {
   const double* u;      // level solution, boundary = g
   View f;               // f at this level's nodes (unused when src is set)
   const double* src;    // NULL, or b given directly on interior nodes: r = LHS(u) + src
-                        // (the adjoint's A lambda = s with lambda's boundary zero)
+                        // (the adjoint's A lambda = s with lambda's boundary zero; MIXED
+                        // refinement steps after the first reuse -RHS(f) from rhs_out)
+  double* rhs_out;      // NULL, or receives -RHS(f) on interior nodes (f path only)
   void* r;              // TR* output
   double tol_b2;        // tol2 = max(tol_b2 * bb, tol_r2 * rr)
   double tol_r2;
