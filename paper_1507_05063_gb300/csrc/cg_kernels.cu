@@ -590,8 +590,15 @@ __device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* 
       break;
     }
     alpha = rr / pq;
-    // K2 body (elementwise: a flat, vectorised partition of the node array)
-    acc = update_flat<T>(d, bl, G, (T)alpha, pnew);
+    // K2 body.  Elementwise: large grids take a flat, vectorised partition of the node
+    // array; grids too small to give every block a full chunk keep the tile partition
+    // (every block busy, one short column each -- lower latency)
+    acc = 0.0;
+    if (d.g.nodes() >= (long long)G * kChunk) {
+      acc = update_flat<T>(d, bl, G, (T)alpha, pnew);
+    } else {
+      for (long long t = bl; t < total_tiles; t += G) acc += (double)update_tile<T>(d, t, (T)alpha, pnew);
+    }
     bs = block_sum(acc);
     if (threadIdx.x == 0) partB[bl] = bs;
     if (!sync_all()) {
