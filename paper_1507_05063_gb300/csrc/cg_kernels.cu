@@ -670,11 +670,10 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
 // K3: r = LHS(u) - RHS(f) = b - A u_I (float64), sums r.r and b.b, CG state init
 // ---------------------------------------------------------------------------------
 template <typename TR>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads)
     k_residual(int nprob, const ResDesc* __restrict__ descs, long long total_tiles,
                CGState* st, double* partials, unsigned* counters) {
   __shared__ double su[2][kTY + 2][kTX + 2];
-  __shared__ double sf[2][kTY + 2][kTX + 2];
   __shared__ int s_active[kMaxProb];
   __shared__ double s_part[2 * kMaxProb];
   for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
@@ -717,9 +716,6 @@ __global__ void __launch_bounds__(kThreads, 3)
     // C/T terms (see k_dir_spmv_dot) of the stencil of u over all 19 nodes, and of its
     // boundary part: b = LHS(boundary part of u) - RHS(f)
     double Cm1 = 0, Tm1 = 0, Tm2 = 0, LCm1 = 0, LTm1 = 0, LTm2 = 0;
-    // right-hand side (6 f_c + 6 face f)/2, split per plane: Fxy_k = 6 f + the 4 in-plane
-    // face values, and the centre values f_{k-1}, f_{k+1} of the neighbouring planes
-    double Fxy_m1 = 0, fc_m1 = 0, fc_m2 = 0;
     const bool use_f = d.src == nullptr;
     for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
       const bool plane_in = (kk >= 0) && (kk <= g.nz);
@@ -727,18 +723,12 @@ __global__ void __launch_bounds__(kThreads, 3)
       for (int idx = threadIdx.x; idx < (kTX + 2) * (kTY + 2); idx += kThreads) {
         const int ly = idx / (kTX + 2), lx = idx - ly * (kTX + 2);
         const int gi = c.x0 - 1 + lx, gj = c.y0 - 1 + ly;
-        double v = 0.0, fv = 0.0;
-        if (plane_in && gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny) {
+        double v = 0.0;
+        if (plane_in && gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny)
           v = u[gi + gj * g.sy + (long long)kk * g.sz];
-          if (use_f) fv = d.f.at(gi, gj, kk);
-        }
         su[buf][ly][lx] = v;
-        sf[buf][ly][lx] = fv;
       }
       __syncthreads();
-      const double fc = sf[buf][ty + 1][tx + 1];
-      const double Fxy = fma(6.0, fc, (sf[buf][ty + 1][tx] + sf[buf][ty + 1][tx + 2]) +
-                                          (sf[buf][ty][tx + 1] + sf[buf][ty + 2][tx + 1]));
       const double P = su[buf][ty + 1][tx + 1];
       const double W = su[buf][ty + 1][tx], E = su[buf][ty + 1][tx + 2];
       const double S = su[buf][ty][tx + 1], N = su[buf][ty + 2][tx + 1];
@@ -767,7 +757,14 @@ __global__ void __launch_bounds__(kThreads, 3)
         const bool interior = inxy && kc > 0 && kc < g.nz;
         double rv = 0.0;
         if (interior) {
-          const double rhs = use_f ? 0.5 * (Fxy_m1 + (fc_m2 + fc)) : -d.src[o];
+          // right-hand side (6 f_c + the 6 face values of f) / 2 of eq. (compact); the
+          // face values are re-read through L1 by the neighbouring threads
+          const View& F = d.f;
+          const double rhs =
+              use_f ? 0.5 * (6.0 * F.at(i, j, kc) + ((F.at(i - 1, j, kc) + F.at(i + 1, j, kc)) +
+                                                     (F.at(i, j - 1, kc) + F.at(i, j + 1, kc)) +
+                                                     (F.at(i, j, kc - 1) + F.at(i, j, kc + 1))))
+                    : -d.src[o];
           if (d.rhs_out) d.rhs_out[o] = -rhs;
           // LHS(u) = -(A-stencil of u over all 19 nodes)
           rv = -((Cm1 + Tm2) + Tk) - rhs;
@@ -785,9 +782,6 @@ __global__ void __launch_bounds__(kThreads, 3)
       LTm2 = LTm1;
       LTm1 = LTk;
       LCm1 = LCk;
-      fc_m2 = fc_m1;
-      fc_m1 = fc;
-      Fxy_m1 = Fxy;
       buf ^= 1;
     }
   }
