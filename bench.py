@@ -60,33 +60,40 @@ ALGO = {
     "update_f64": {"bytes": 48.0, "dp_ops": 3.0},    # x, p, r, q in; x, r out
     "spmv_f32": {"bytes": 16.0, "dp_ops": 0.0},
     "update_f32": {"bytes": 24.0, "dp_ops": 0.0},
-    # u, f in; r out.  DP ops: 19-point sum 12 + combine 3, RHS 7, r.r 1, b and b.b 4
-    "residual": {"bytes": 24.0, "dp_ops": 27.0},
-    # per fine node: ~5.5 FMA for the three quartic passes + the extrapolated lattice
-    "exp_finite": {"bytes": 8.0 * (1 + 1 / 8 + 1 / 64), "dp_ops": 6.0},
+    # u, f in; r out.  DP ops: per plane 12 (19-point C/T terms), per node 2 (combine),
+    # 6 (twice the RHS), 1 (r), 1 (r.r), 1 (b.b; the lift terms only near the boundary)
+    "residual": {"bytes": 24.0, "dp_ops": 23.0},
+    # per fine node: ~4.4 FMA for the three quartic passes (odd positions only), ~1 for
+    # the extrapolated lattice (separable corner sums + one FMA per grid-2h node)
+    "exp_finite": {"bytes": 8.0 * (1 + 1 / 8 + 1 / 64), "dp_ops": 5.4},
     "init": {"bytes": 8.0, "dp_ops": 0.0},
     "correct": {"bytes": 24.0, "dp_ops": 1.0},
     "exp_true": {"bytes": 8.0 * (2 + 1 / 8), "dp_ops": 4.0},
     # persistent CG: per node and CG step (the two fused bodies above)
     "cg_f64": {"bytes": 80.0, "dp_ops": 19.0},
     "cg_f32": {"bytes": 40.0, "dp_ops": 0.0},
-    # single-block CG of a small grid: vectors live in shared memory
-    "cg_small_f64": {"bytes": 0.0, "dp_ops": 30.0},
-    "cg_small_f32": {"bytes": 0.0, "dp_ops": 0.0},
+    # all CG steps of a small grid in one thread-block cluster, vectors in shared memory
+    # (single-reduction recurrence): per node-step p, s, x, r 4 + stencil 19 + r.r, w.r 2
+    "cg_cluster_f64": {"bytes": 0.0, "dp_ops": 25.0},
+    "cg_cluster_f32": {"bytes": 0.0, "dp_ops": 0.0},
+    # all CG steps of a mid-size grid, vectors resident in the blocks' shared memory: the
+    # same 25 operations; global traffic = the published r, s, w of every node (24 B)
+    "cg_resident_f64": {"bytes": 24.0, "dp_ops": 25.0},
 }
 KERNEL_SYMBOL = {"spmv_f64": "k_dir_spmv_dot<double>", "update_f64": "k_update_dot<double>",
                  "spmv_f32": "k_dir_spmv_dot<float>", "update_f32": "k_update_dot<float>",
                  "residual": "k_residual", "exp_finite": "k_exp_finite", "init": "k_boundary_init",
                  "correct": "k_add_correction", "exp_true": "k_exp_true",
                  "cg_f64": "k_cg_persistent<double>", "cg_f32": "k_cg_persistent<float>",
-                 "cg_small_f64": "k_cg_small<double>", "cg_small_f32": "k_cg_small<float>"}
+                 "cg_cluster_f64": "k_cg_cluster<double>", "cg_cluster_f32": "k_cg_cluster<float>",
+                 "cg_resident_f64": "k_cg_resident"}
 KERNEL_SOURCE = {"spmv_f64": "cg_kernels.cu", "update_f64": "cg_kernels.cu",
                  "spmv_f32": "cg_kernels.cu", "update_f32": "cg_kernels.cu",
                  "residual": "cg_kernels.cu", "exp_finite": "transfer_kernels.cu",
                  "init": "transfer_kernels.cu", "correct": "cg_kernels.cu",
                  "exp_true": "transfer_kernels.cu", "cg_f64": "cg_kernels.cu",
-                 "cg_f32": "cg_kernels.cu", "cg_small_f64": "cg_kernels.cu",
-                 "cg_small_f32": "cg_kernels.cu"}
+                 "cg_f32": "cg_kernels.cu", "cg_cluster_f64": "cluster_cg.cu",
+                 "cg_cluster_f32": "cluster_cg.cu", "cg_resident_f64": "resident_cg.cu"}
 # FP64 issue rate: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz (maximum SM clock).
 DP_PEAK_GOPS = 2 * 152 * 2.070
 

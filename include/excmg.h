@@ -68,9 +68,11 @@ typedef enum {
   EXCMG_K_CG_F64 = 9,     /* all CG steps of a level in one persistent launch (float64);
                              prof_nodes counts nodes x steps */
   EXCMG_K_CG_F32 = 10,    /* the same for a float32 inner solve */
-  EXCMG_K_CG_SMALL_F64 = 11, /* all CG steps of a small grid in one block (float64) */
-  EXCMG_K_CG_SMALL_F32 = 12, /* the same in float32 */
-  EXCMG_KERNEL_KINDS = 13
+  EXCMG_K_CG_CLUSTER_F64 = 11, /* all CG steps of a small grid in one block cluster (float64) */
+  EXCMG_K_CG_CLUSTER_F32 = 12, /* the same in float32 */
+  EXCMG_K_CG_RESIDENT_F64 = 13, /* all CG steps of a mid-size grid, vectors resident in the
+                                   blocks' shared memory (float64) */
+  EXCMG_KERNEL_KINDS = 14
 } excmg_kernel_kind;
 
 /* Box and grids (Section 2: hx = Lx/Nx ...; Algorithm 1: coarsest grid H, L levels). */

@@ -684,19 +684,20 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   int buf = 0, cur = -1, p = 0;
-  double acc_r = 0.0, acc_b = 0.0;
+  // acc_b4 sums (2 b)^2 over nodes whose stencil misses the boundary (there b = -RHS)
+  double acc_r = 0.0, acc_b = 0.0, acc_b4 = 0.0;
   for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
     p = find_problem(descs, nprob, t, p);
     if (p != cur) {
       if (cur >= 0) {
         const double s1 = block_sum(acc_r);
-        const double s2 = block_sum(acc_b);
+        const double s2 = block_sum(fma(0.25, acc_b4, acc_b));
         if (threadIdx.x == 0) {
           s_part[2 * cur] += s1;
           s_part[2 * cur + 1] += s2;
         }
       }
-      acc_r = acc_b = 0.0;
+      acc_r = acc_b = acc_b4 = 0.0;
       cur = p;
     }
     const ResDesc& d = descs[p];
@@ -711,23 +712,40 @@ __global__ void __launch_bounds__(kThreads)
     const bool perim = inxy && (i == 1 || i == g.nx - 1 || j == 1 || j == g.ny - 1);
     // which of the 3x3 neighbour columns are boundary columns
     const bool bxm = (i - 1 == 0), bxp = (i + 1 == g.nx), bym = (j - 1 == 0), byp = (j + 1 == g.ny);
+    const bool deep = inxy && !perim;  // no boundary node in this column's 3x3 neighbourhood
     const bool want_b = d.want_b != 0;
     const Coef A = d.A;
     // C/T terms (see k_dir_spmv_dot) of the stencil of u over all 19 nodes, and of its
     // boundary part: b = LHS(boundary part of u) - RHS(f)
     double Cm1 = 0, Tm1 = 0, Tm2 = 0, LCm1 = 0, LTm1 = 0, LTm2 = 0;
     const bool use_f = d.src == nullptr;
-    for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
-      const bool plane_in = (kk >= 0) && (kk <= g.nz);
-      const bool plane_bnd = (kk == 0) || (kk == g.nz);
-      for (int idx = threadIdx.x; idx < (kTX + 2) * (kTY + 2); idx += kThreads) {
+    // the (kTX+2) x (kTY+2) plane of u, at most two elements per thread; the loads of
+    // plane kk+1 are issued before the barrier and arithmetic of plane kk
+    auto load_u = [&](int kk, double& a0, double& a1) {
+      a0 = a1 = 0.0;
+      if (kk < 0 || kk > g.nz) return;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int idx = threadIdx.x + h * kThreads;
+        if (idx >= kStage) break;
         const int ly = idx / (kTX + 2), lx = idx - ly * (kTX + 2);
         const int gi = c.x0 - 1 + lx, gj = c.y0 - 1 + ly;
-        double v = 0.0;
-        if (plane_in && gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny)
-          v = u[gi + gj * g.sy + (long long)kk * g.sz];
-        su[buf][ly][lx] = v;
+        if (gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny) {
+          const double v = u[gi + gj * g.sy + (long long)kk * g.sz];
+          if (h == 0) a0 = v; else a1 = v;
+        }
       }
+    };
+    double n0, n1;
+    load_u(c.z0 - 1, n0, n1);
+    for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
+      const bool plane_bnd = (kk == 0) || (kk == g.nz);
+      {
+        double* flat = &su[buf][0][0];
+        flat[threadIdx.x] = n0;
+        if (threadIdx.x + kThreads < kStage) flat[threadIdx.x + kThreads] = n1;
+      }
+      if (kk < c.z1) load_u(kk + 1, n0, n1);
       __syncthreads();
       const double P = su[buf][ty + 1][tx + 1];
       const double W = su[buf][ty + 1][tx], E = su[buf][ty + 1][tx + 2];
@@ -754,24 +772,28 @@ __global__ void __launch_bounds__(kThreads)
       const int kc = kk - 1;
       if (kc >= c.z0 && own) {
         const long long o = i + j * g.sy + (long long)kc * g.sz;
-        const bool interior = inxy && kc > 0 && kc < g.nz;
         double rv = 0.0;
-        if (interior) {
-          // right-hand side (6 f_c + the 6 face values of f) / 2 of eq. (compact); the
-          // face values are re-read through L1 by the neighbouring threads
+        if (inxy && kc > 0 && kc < g.nz) {
+          // twice the right-hand side of eq. (compact), 6 f_c + the 6 face values of f (the
+          // face values are re-read through L1 by the neighbouring threads); the factor
+          // 1/2 is applied inside the fused multiply-adds below, exactly
           const View& F = d.f;
-          const double rhs =
-              use_f ? 0.5 * (6.0 * F.at(i, j, kc) + ((F.at(i - 1, j, kc) + F.at(i + 1, j, kc)) +
-                                                     (F.at(i, j - 1, kc) + F.at(i, j + 1, kc)) +
-                                                     (F.at(i, j, kc - 1) + F.at(i, j, kc + 1))))
-                    : -d.src[o];
-          if (d.rhs_out) d.rhs_out[o] = -rhs;
-          // LHS(u) = -(A-stencil of u over all 19 nodes)
-          rv = -((Cm1 + Tm2) + Tk) - rhs;
+          const double rhs2 =
+              use_f ? fma(6.0, F.at(i, j, kc), ((F.at(i - 1, j, kc) + F.at(i + 1, j, kc)) +
+                                                (F.at(i, j - 1, kc) + F.at(i, j + 1, kc)) +
+                                                (F.at(i, j, kc - 1) + F.at(i, j, kc + 1))))
+                    : -2.0 * d.src[o];
+          if (d.rhs_out) d.rhs_out[o] = -0.5 * rhs2;
+          // LHS(u) - RHS = -(A-stencil of u over all 19 nodes) - RHS
+          rv = fma(-0.5, rhs2, -((Cm1 + Tm2) + Tk));
           acc_r = fma(rv, rv, acc_r);
           if (want_b) {
-            const double bv = -((LCm1 + LTm2) + LTk) - rhs;
-            acc_b = fma(bv, bv, acc_b);
+            if (deep && kc >= 2 && kc <= g.nz - 2) {
+              acc_b4 = fma(rhs2, rhs2, acc_b4);  // b = -RHS here
+            } else {
+              const double bv = fma(-0.5, rhs2, -((LCm1 + LTm2) + LTk));
+              acc_b = fma(bv, bv, acc_b);
+            }
           }
         }
         rout[o] = (TR)rv;
@@ -787,7 +809,7 @@ __global__ void __launch_bounds__(kThreads)
   }
   if (cur >= 0) {
     const double s1 = block_sum(acc_r);
-    const double s2 = block_sum(acc_b);
+    const double s2 = block_sum(fma(0.25, acc_b4, acc_b));
     if (threadIdx.x == 0) {
       s_part[2 * cur] += s1;
       s_part[2 * cur + 1] += s2;
@@ -844,120 +866,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// ---------------------------------------------------------------------------------
-// Small-grid CG: one block holds x, r, p, q of the whole grid in shared memory and runs
-// every CG step with block barriers only (no global round trip per step).  Worth it
-// while one SM's float64 rate beats the multi-block kernel's per-step latency: grids
-// of up to kSmallNodes nodes.
-// ---------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kSmallThreads)
-    k_cg_small(const CGDesc<T>* __restrict__ descs, CGState* st) {
-  extern __shared__ __align__(16) unsigned char s_raw[];
-  __shared__ double s_red[1];
-  __shared__ double s_park[kSmallThreads];
-  const CGDesc<T>& d = descs[0];
-  CGState* S = st + d.slot;
-  if (S->done) return;
-  const Grid3 g = d.g;
-  const int n = (int)g.nodes();
-  T* xs = reinterpret_cast<T*>(s_raw);
-  T* rs = xs + n;
-  T* ps = rs + n;
-  T* qs = ps + n;
-  const int sy = (int)g.sy, sz = (int)g.sz;
-  for (int o = threadIdx.x; o < n; o += blockDim.x) {
-    xs[o] = d.x[o];
-    rs[o] = d.r[o];
-    ps[o] = T(0);
-    qs[o] = T(0);
-  }
-  const T c0 = (T)d.A.c0, fx = (T)d.A.fx, fy = (T)d.A.fy, fz = (T)d.A.fz;
-  const T exy = (T)d.A.exy, exz = (T)d.A.exz, eyz = (T)d.A.eyz;
-  double rr = S->rr, beta = S->first ? 0.0 : S->beta, pq = 0.0, alpha = 0.0;
-  const double tol2 = S->tol2;
-  int iter = S->iter;
-  const int max_iter = S->max_iter, fixed = S->fixed;
-  int status = EXCMG_OK;
-  // block reduction: values parked in shared memory, float64 adds by warp 0 only, the
-  // result broadcast through shared memory (fixed order: deterministic)
-  auto reduce = [&](double v) -> double {
-    __syncthreads();
-    s_park[threadIdx.x] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double t = 0.0;
-      for (int k = threadIdx.x; k < kSmallThreads; k += 32) t += s_park[k];
-      t = warp_sum(t);
-      if (threadIdx.x == 0) s_red[0] = t;
-    }
-    __syncthreads();
-    return s_red[0];
-  };
-  __syncthreads();
-  for (;;) {
-    for (int o = threadIdx.x; o < n; o += blockDim.x) ps[o] = fmaT((T)beta, ps[o], rs[o]);
-    __syncthreads();
-    double acc = 0.0;
-    for (int o = threadIdx.x; o < n; o += blockDim.x) {
-      const int i = o % sy, j = (o / sy) % (g.ny + 1), k = o / sz;
-      T qv = T(0);
-      if (i > 0 && i < g.nx && j > 0 && j < g.ny && k > 0 && k < g.nz) {
-        const T* P = ps + o;
-        const T SX = P[-1] + P[1], SY = P[-sy] + P[sy], SZ = P[-sz] + P[sz];
-        const T EXY = (P[-1 - sy] + P[1 - sy]) + (P[-1 + sy] + P[1 + sy]);
-        const T EXZ = (P[-1 - sz] + P[1 - sz]) + (P[-1 + sz] + P[1 + sz]);
-        const T EYZ = (P[-sy - sz] + P[sy - sz]) + (P[-sy + sz] + P[sy + sz]);
-        qv = fmaT(c0, P[0], fmaT(fx, SX, fmaT(fy, SY, fmaT(fz, SZ, fmaT(exy, EXY, fmaT(exz, EXZ, eyz * EYZ))))));
-        acc += (double)(P[0] * qv);
-      }
-      qs[o] = qv;
-    }
-    pq = reduce(acc);
-    if (pq == 0.0 && rr == 0.0) break;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      status = EXCMG_ERR_NONFINITE;
-      break;
-    }
-    alpha = rr / pq;
-    acc = 0.0;
-    for (int o = threadIdx.x; o < n; o += blockDim.x) {
-      xs[o] = fmaT((T)alpha, ps[o], xs[o]);
-      const T rv = fmaT((T)-alpha, qs[o], rs[o]);
-      rs[o] = rv;
-      acc += (double)(rv * rv);
-    }
-    const double rrn = reduce(acc);
-    beta = (rr > 0.0) ? rrn / rr : 0.0;
-    rr = rrn;
-    iter += 1;
-    if (!isfinite(rr)) {
-      status = EXCMG_ERR_NONFINITE;
-      break;
-    }
-    if (rr <= tol2) break;
-    if (iter >= max_iter) {
-      if (!fixed) status = EXCMG_ERR_NOT_CONVERGED;
-      break;
-    }
-  }
-  __syncthreads();
-  for (int o = threadIdx.x; o < n; o += blockDim.x) {
-    d.x[o] = xs[o];
-    d.r[o] = rs[o];
-  }
-  if (threadIdx.x == 0) {
-    S->rr = rr;
-    S->pq = pq;
-    S->alpha = alpha;
-    S->beta = beta;
-    S->iter = iter;
-    S->first = 0;
-    S->status = status;
-    S->done = 1;
-  }
-}
-
 int g_max_grid = 0;
 int g_coop_grid[2] = {0, 0};  // co-resident blocks of k_cg_persistent<double>, <float>
 
@@ -978,23 +886,6 @@ int persistent_cg_blocks() {
 }
 template int persistent_cg_blocks<double>();
 template int persistent_cg_blocks<float>();
-
-template <typename T>
-cudaError_t launch_cg_small(const CGDesc<T>* descs, long long nodes, CGState* st, cudaStream_t s) {
-  const size_t smem = 4 * sizeof(T) * (size_t)nodes;
-  static bool attr_set[2] = {false, false};
-  bool& set = attr_set[sizeof(T) == 8 ? 0 : 1];
-  if (!set) {
-    cudaError_t e = cudaFuncSetAttribute(k_cg_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(4 * sizeof(T) * kSmallNodes));
-    if (e != cudaSuccess) return e;
-    set = true;
-  }
-  k_cg_small<T><<<1, kSmallThreads, smem, s>>>(descs, st);
-  return cudaGetLastError();
-}
-template cudaError_t launch_cg_small<double>(const CGDesc<double>*, long long, CGState*, cudaStream_t);
-template cudaError_t launch_cg_small<float>(const CGDesc<float>*, long long, CGState*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_cg_persistent(int nprob, const CGDesc<T>* descs, int grid, CGState* st,

@@ -47,6 +47,7 @@ Tiling make_tiling(const Grid3& g, int tz) {
   return t;
 }
 
+
 // Slab depth: among 1..64 the one minimising (waves of tiles) x (planes staged per tile),
 // a model of the stencil kernel's time when every block runs at the same rate.  Large
 // grids get deep slabs (little halo re-staging); small, latency-bound grids get thin
@@ -130,6 +131,7 @@ struct ProbLayout {
   size_t r, pa, pb, q;                  // float64 CG vectors (finest size)
   size_t r32, pa32, pb32, q32, e32;     // float32 CG vectors (MIXED)
   size_t rhs64;                         // MIXED: -RHS(f) of the level being refined
+  size_t s0, s1;                        // resident CG: s by step parity (its grids' size)
   size_t bytes;
 };
 
@@ -160,6 +162,17 @@ ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_
     off = align_up(off + sizeof(double) * n64);
     L.q = off;
     off = align_up(off + sizeof(double) * n64);
+    // two more float64 vectors for the levels small enough for the resident CG
+    long long nres = 0;
+    for (const Level& l : lv)
+      if (l.nodes() <= kResidentMaxNodes && (!mixed || need_fp64_vectors || l.nodes() < minn))
+        nres = std::max(nres, l.nodes());
+    if (nres > 0) {
+      L.s0 = off;
+      off = align_up(off + sizeof(double) * nres);
+      L.s1 = off;
+      off = align_up(off + sizeof(double) * nres);
+    }
   }
   if (mixed) {
     L.r32 = off;
@@ -329,13 +342,71 @@ template <typename T>
 excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int grid,
                      const std::vector<int>& slots, int nslots, int chunk0,
                      std::vector<CGState>& hs, double nodes, std::vector<CGDesc<T>>& hd) {
-  // Every problem runs all its CG steps inside one cooperative launch when the device
-  // supports it (and the barrier count cannot wrap): problem p gets a block range
-  // proportional to its tiles and iterates on its own.  A single small grid runs in one
-  // block with its vectors in shared memory.
+  // Every problem runs all its CG steps inside one launch when the device supports it:
+  // small grids (all of this phase's problems up to kClusterMaxNodes nodes) each in one
+  // thread-block cluster with the vectors in shared memory; larger ones in a cooperative
+  // launch where problem p gets a team of blocks and iterates on its own.
   const int coop = persistent_cg_blocks<T>();
+  // a single float64 grid that fits the resident CG (vectors in shared memory)
+  // (grids small enough for one cluster stay on the cluster kernel below: its exchange
+  // through distributed shared memory beats the global round trips of the resident one)
+  if (n == 1 && sizeof(T) == 8 && c.persistent_ok && hd[0].s0 && hd[0].s1 &&
+      hd[0].g.nodes() > kClusterMaxNodes && hd[0].g.nodes() <= kResidentMaxNodes) {
+    ResidentDesc D;
+    memset(&D, 0, sizeof(D));
+    size_t smem = 0;
+    if (resident_box(hd[0].g, D, smem)) {
+      D.g = hd[0].g;
+      D.A = hd[0].A;
+      D.slot = hd[0].slot;
+      D.x = reinterpret_cast<double*>(hd[0].x);
+      D.r = reinterpret_cast<double*>(hd[0].r);
+      D.r1 = reinterpret_cast<double*>(hd[0].pa);
+      D.w0 = reinterpret_cast<double*>(hd[0].pb);
+      D.w1 = reinterpret_cast<double*>(hd[0].q);
+      D.s0 = reinterpret_cast<double*>(hd[0].s0);
+      D.s1 = reinterpret_cast<double*>(hd[0].s1);
+      double2* pairs = reinterpret_cast<double2*>(c.partials());  // 2 G pairs
+      CK(cudaMemsetAsync(c.bar(), 0, 2 * sizeof(unsigned), c.s));  // counter, time-out flag
+      if (c.launches) *c.launches += 1;
+      if (c.prof) {
+        const size_t a = c.prof->event(), b = c.prof->event();
+        if (c.prof->pool[a]) cudaEventRecord(c.prof->pool[a], c.s);
+        CK(launch_cg_resident(D, smem, c.st(), pairs, c.bar(), c.bar_err(), c.s));
+        if (c.prof->pool[b]) cudaEventRecord(c.prof->pool[b], c.s);
+        c.prof->recs.push_back({EXCMG_K_CG_RESIDENT_F64, a, b, nodes, true, slots[0]});
+      } else {
+        CK(launch_cg_resident(D, smem, c.st(), pairs, c.bar(), c.bar_err(), c.s));
+      }
+      if (c.defer) return EXCMG_OK;
+      excmg_status e = read_states(c, nslots, hs);
+      if (e == EXCMG_OK && c.prof) {
+        // states are read now: count the steps before a later residual resets them
+        Prof::Rec& rec = c.prof->recs.back();
+        rec.nodes *= hs[slots[0]].iter;
+        rec.iter_slot = -1;
+        rec.real = hs[slots[0]].iter > 0;
+      }
+      return e;
+    }
+  }
   if (coop >= n && coop > 0 && c.persistent_ok) {
-    const bool small = n == 1 && nodes <= (double)kSmallNodes;
+    int csize = 0;
+    size_t csmem = 0;
+    for (int p = 0; p < n; ++p) {
+      const int cp = hd[p].g.nodes() <= kClusterMaxNodes ? cluster_cg_size<T>(hd[p].g) : 0;
+      if (cp == 0) {
+        csize = 0;
+        break;
+      }
+      csize = std::max(csize, cp);
+    }
+    long long cmax = 0;
+    for (int p = 0; p < n && csize > 0; ++p) {
+      csmem = std::max(csmem, cluster_cg_smem(hd[p].g, csize, sizeof(T)));
+      cmax = std::max(cmax, hd[p].g.nodes());
+    }
+    const bool small = csize > 0;
     int grid_total = 0;
     if (!small) {
       // team sizes: a lone problem takes every co-resident block it can use; in a batch
@@ -362,10 +433,10 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
       CK(cudaMemsetAsync(c.bar(), 0, (2 * sizeof(unsigned)) * n + sizeof(unsigned), c.s));
     }
     auto launch = [&]() -> cudaError_t {
-      if (small) return launch_cg_small<T>(ddesc, (long long)nodes, c.st(), c.s);
+      if (small) return launch_cg_cluster<T>(n, ddesc, csize, csmem, cmax, c.st(), c.s);
       return launch_cg_persistent<T>(n, ddesc, grid_total, c.st(), c.partials(), c.bar(), c.s);
     };
-    const int kind = small ? (sizeof(T) == 8 ? EXCMG_K_CG_SMALL_F64 : EXCMG_K_CG_SMALL_F32)
+    const int kind = small ? (sizeof(T) == 8 ? EXCMG_K_CG_CLUSTER_F64 : EXCMG_K_CG_CLUSTER_F32)
                            : (sizeof(T) == 8 ? EXCMG_K_CG_F64 : EXCMG_K_CG_F32);
     if (c.launches) *c.launches += 1;
     if (c.prof && n == 1) {
@@ -643,6 +714,9 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   d.pa = reinterpret_cast<double*>(p.base + p.L.pa);
   d.pb = reinterpret_cast<double*>(p.base + p.L.pb);
   d.q = reinterpret_cast<double*>(p.base + p.L.q);
+  const bool res = p.L.s1 > 0 && g.nodes() <= kResidentMaxNodes;
+  d.s0 = res ? reinterpret_cast<double*>(p.base + p.L.s0) : nullptr;
+  d.s1 = res ? reinterpret_cast<double*>(p.base + p.L.s1) : nullptr;
   d.aux = nullptr;
   CGDesc<float>& f = it.d32;
   f.g = g;
@@ -654,6 +728,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   f.pa = reinterpret_cast<float*>(p.base + p.L.pa32);
   f.pb = reinterpret_cast<float*>(p.base + p.L.pb32);
   f.q = reinterpret_cast<float*>(p.base + p.L.q32);
+  f.s0 = f.s1 = nullptr;
   f.aux = p.level_u(l);
   f.scale = 1.0;
   it.rhs_cache = p.L.rhs64 ? reinterpret_cast<double*>(p.base + p.L.rhs64) : nullptr;

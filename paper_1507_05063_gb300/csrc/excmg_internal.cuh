@@ -19,8 +19,11 @@ constexpr int kThreads = 256;    // threads of every tiled kernel
 constexpr int kTX = 32;          // x-width of a stencil tile (one warp)
 constexpr int kTY = 8;           // y-rows of a stencil tile
 constexpr int kMaxGrid = 4096;   // cap on persistent grid size (partials per problem)
-constexpr int kSmallNodes = 1536;  // grids up to this many nodes: single-block CG
-constexpr int kSmallThreads = 128;
+#ifndef EXCMG_CLUSTER_MAX_NODES
+#define EXCMG_CLUSTER_MAX_NODES 20000
+#endif
+// grids up to this many nodes run all their CG steps in one thread-block cluster
+constexpr long long kClusterMaxNodes = EXCMG_CLUSTER_MAX_NODES;
 // MIXED mode solves grids below this many nodes in float64 by default: there CG is
 // latency-bound, float32 saves nothing and refinement would add host round trips.
 constexpr long long kMixedMinNodes = 1LL << 21;
@@ -88,6 +91,8 @@ struct CGDesc {
   T* pa;                  // p buffers: even steps read pa and write pb, odd steps swap
   T* pb;
   T* q;
+  T* s0;                  // resident CG (float64 grids up to kResidentMaxNodes): s by
+  T* s1;                  //   step parity (NULL elsewhere)
   double* aux;            // MIXED inner solve: the float64 level solution u += x / scale
   double scale;           // MIXED inner solve: it solves A x = scale * r (r scaled to O(1)
                           // so float32 products neither underflow nor overflow)
@@ -145,13 +150,46 @@ int persistent_grid(long long total_tiles);
 // cooperative launch.
 template <typename T>
 int persistent_cg_blocks();
-// All CG steps of ONE problem of at most kSmallNodes nodes in one block, with x, r, p, q
-// in shared memory.
+// All CG steps of each problem in one thread-block cluster of `csize` CTAs (grid =
+// nprob clusters), x, r, p, q in the cluster's shared memory (cluster_cg.cu).
+// cluster_cg_size: the cluster size for grid g (1..16), or 0 if g does not fit or the
+// device cannot launch it; cluster_cg_smem: dynamic shared memory per CTA for g at csize.
 template <typename T>
-cudaError_t launch_cg_small(const CGDesc<T>* descs, long long nodes, CGState* st, cudaStream_t s);
+int cluster_cg_size(const Grid3& g);
+size_t cluster_cg_smem(const Grid3& g, int csize, size_t elem);
+template <typename T>
+cudaError_t launch_cg_cluster(int nprob, const CGDesc<T>* descs, int csize, size_t smem,
+                              long long max_nodes, CGState* st, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cg_persistent(int nprob, const CGDesc<T>* descs, int grid, CGState* st,
                                  double* partials, unsigned* bar, cudaStream_t s);
+
+// All CG steps of ONE float64 grid of up to kResidentMaxNodes nodes in a cooperative
+// grid whose blocks keep the level's vectors in shared memory (resident_cg.cu).
+#ifndef EXCMG_RESIDENT_MAX_NODES
+#define EXCMG_RESIDENT_MAX_NODES (1 << 19)
+#endif
+constexpr long long kResidentMaxNodes = EXCMG_RESIDENT_MAX_NODES;
+struct ResidentDesc {
+  Grid3 g;
+  Coef A;
+  int slot;               // CGState of the problem
+  int bx, by, bz;         // interior nodes per box
+  int nbx, nby, nbz;      // boxes per direction (grid = their product)
+  double* x;              // level solution (boundary = g)
+  double* r;              // residual r_0 in, last r out; also the even-step copy of r
+  double* r1;             // odd-step copy of r
+  double* w0;             // w = A r, even / odd steps
+  double* w1;
+  double* s0;             // s, even / odd steps
+  double* s1;
+};
+// Chooses the boxes for grid g; false if the grid does not fit or the device has no
+// cooperative launch.  smem: dynamic shared memory per block.
+bool resident_box(const Grid3& g, ResidentDesc& D, size_t& smem);
+// pairs: 2 G double2 (G = nbx nby nbz); counter, err: zeroed.
+cudaError_t launch_cg_resident(const ResidentDesc& D, size_t smem, CGState* st, double2* pairs,
+                               unsigned* counter, int* err, cudaStream_t s);
 
 // Transfer kernels (transfer_kernels.cu).
 struct ProlongDesc {

@@ -1,0 +1,458 @@
+// Level CG with the level's vectors resident in shared memory, for one grid of up to a
+// few hundred thousand nodes (the middle levels of the cascade, where a CG step is bound
+// by latency, not by the FP64 pipe or HBM).
+//
+// A cooperative grid of G blocks; block b owns a box of BX x BY x BZ interior nodes and
+// keeps in shared memory, for all steps of the level, x, p, s, w of its box and r of its
+// box plus a one-node halo.  The recurrence is the single-reduction form of CG of
+// Chronopoulos and Gear (1989), as in the cluster kernel:
+//
+//    p = r + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,
+//    w = A r,  gamma = r.r,  delta = w.r   (one grid reduction for both),
+//    beta' = gamma' / gamma,  alpha' = gamma' / (delta' - beta' gamma' / alpha);
+//
+// in exact arithmetic x and r are those of the standard recurrence (the smoother of
+// Algorithm 1), and the loop stops on the same recursive residual r.r <= tol2.
+//
+// Halo exchange through global memory (L2): every step each block publishes the new r, s
+// and w of its box into node arrays of the level (two copies by step parity), and the
+// next step recomputes the new r on its halo from its neighbours' published r, w, s with
+// the same fused operations as the owner (bit-identical).  So one step needs one grid-wide
+// synchronisation, the reduction's: per-block partials, one arrival counter (release /
+// acquire, bounded wait: EXCMG_ERR_TIMEOUT), then every block adds the G partials in
+// index order, so all blocks hold bit-identical scalars and take the same decisions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "excmg_internal.cuh"
+
+namespace excmg {
+namespace {
+
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr unsigned long long kRsSpinLimit = 1ull << 25;
+constexpr int kRsHB = 6;  // halo nodes per thread whose loads are issued ahead
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ double rs_xor_sum(double v, int from) {
+  for (int o = from; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Grid-wide sums of (a, b) over every thread of every block, in *s_out of every block
+// (bit-identical).  Reduction number `seq` (1, 2, ...): block b stores its partials into
+// pair b of the set seq & 1 (two sets: a block can be one reduction ahead of another's
+// reads, never two), arrives on the counter with release semantics and waits (bounded)
+// until all G blocks have arrived; then warp 0 adds the G pairs in index order.
+// Returns false if the wait ran out or another block reported a time-out.
+__device__ bool rs_grid_sum2(double a, double b, double2* pairs, unsigned* counter, int G,
+                             unsigned seq, int* err, double* s_warp, double2* s_out, int* s_ok) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a = rs_xor_sum(a, 16);
+  b = rs_xor_sum(b, 16);
+  if (lane == 0) {
+    s_warp[warp] = a;
+    s_warp[kRsWarps + warp] = b;
+  }
+  __syncthreads();
+  double2* set = pairs + (size_t)(seq & 1) * G;
+  if (warp == 0) {
+    double ta = lane < kRsWarps ? s_warp[lane] : 0.0;
+    double tb = lane < kRsWarps ? s_warp[kRsWarps + lane] : 0.0;
+    ta = rs_xor_sum(ta, kRsWarps / 2);
+    tb = rs_xor_sum(tb, kRsWarps / 2);
+    if (lane == 0) {
+      __stcg(&set[blockIdx.x], make_double2(ta, tb));
+      // release: this block's partials and (through the block barrier above) every
+      // store of its threads become visible before the arrival
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
+      const unsigned target = seq * (unsigned)G;
+      int ok = 1;
+      unsigned long long spins = 0;
+      while (ld_acquire_u32(counter) < target) {
+        if (++spins > kRsSpinLimit || *(volatile int*)err) {
+          ok = 0;
+          break;
+        }
+        if (spins > 4096) __nanosleep(64);
+      }
+      if (!ok) atomicExch(err, 1);
+      *s_ok = ok;
+    }
+    __syncwarp();
+    double sa = 0.0, sb = 0.0;
+    if (*(volatile int*)s_ok) {
+      for (int i = lane; i < G; i += 32) {
+        const double2 v = __ldcg(&set[i]);
+        sa += v.x;
+        sb += v.y;
+      }
+    }
+    sa = rs_xor_sum(sa, 16);
+    sb = rs_xor_sum(sb, 16);
+    if (lane == 0) *s_out = make_double2(sa, sb);
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// 19-point A-stencil at offset 0 of P with strides (1, ey, ez).
+__device__ __forceinline__ double rs_stencil(const double* P, int ey, int ez, const Coef& A) {
+  const double SX = P[-1] + P[1], SY = P[-ey] + P[ey], SZ = P[-ez] + P[ez];
+  const double EXY = (P[-1 - ey] + P[1 - ey]) + (P[-1 + ey] + P[1 + ey]);
+  const double EXZ = (P[-1 - ez] + P[1 - ez]) + (P[-1 + ez] + P[1 + ez]);
+  const double EYZ = (P[-ey - ez] + P[ey - ez]) + (P[-ey + ez] + P[ey + ez]);
+  return fma(A.c0, P[0], fma(A.fx, SX, fma(A.fy, SY, fma(A.fz, SZ, fma(A.exy, EXY, fma(A.exz, EXZ, A.eyz * EYZ))))));
+}
+
+__global__ void __launch_bounds__(kRsThreads)
+    k_cg_resident(const ResidentDesc D, CGState* st, double2* pairs, unsigned* counter, int* err) {
+  extern __shared__ __align__(16) double s_vec[];
+  __shared__ double s_warp[2 * kRsWarps];
+  __shared__ double2 s_red;
+  __shared__ int s_ok;
+  __shared__ double s_alpha, s_beta;
+  __shared__ int s_stop;
+  CGState* S = st + D.slot;
+  if (S->done) return;  // identical in every block: the state is written after the last wait
+  const Grid3 g = D.g;
+  const int G = gridDim.x;
+  const int BX = D.bx, BY = D.by, BZ = D.bz;
+  const int EX = BX + 2, EY = BY + 2, EZ = BZ + 2;
+  const int B = BX * BY * BZ, ext = EX * EY * EZ;
+  const int b = blockIdx.x;
+  const int ibx = b % D.nbx, iby = (b / D.nbx) % D.nby, ibz = b / (D.nbx * D.nby);
+  // global node of box-local (0, 0, 0); the halo starts one node before
+  const int i0 = 1 + ibx * BX, j0 = 1 + iby * BY, k0 = 1 + ibz * BZ;
+  double* R = s_vec;  // ext: (lx+1) + EX (ly+1) + EX EY (lz+1)
+  double* X = R + ext;
+  double* P = X + B;
+  double* Sv = P + B;
+  double* W = Sv + B;
+  const Coef A = D.A;
+  // own node q of the box: its index in R and in the level's node array; valid = the
+  // node exists (boxes at the far faces of the grid may be partial)
+  struct Own {
+    int e;
+    bool valid;
+    long long o;
+  };
+  auto own_node = [&](int q) -> Own {
+    const int lx = q % BX, ly = (q / BX) % BY, lz = q / (BX * BY);
+    const int gi = i0 + lx, gj = j0 + ly, gk = k0 + lz;
+    Own w;
+    w.e = (lx + 1) + EX * ((ly + 1) + EY * (lz + 1));
+    w.o = gi + gj * g.sy + (long long)gk * g.sz;
+    w.valid = gi < g.nx && gj < g.ny && gk < g.nz;
+    return w;
+  };
+  // shell position h (0 .. ext - B - 1): the 2 z-faces, then the 2 y-faces, then the 2
+  // x-faces of the extended box
+  const int zf = EX * EY, yf = EX * BZ, xf = BY * BZ;
+  const int nshell = 2 * (zf + yf + xf);
+  auto shell_node = [&](int h, int& e, int& gi, int& gj, int& gk) {
+    int ex, ey, ez;
+    if (h < 2 * zf) {
+      ez = h < zf ? 0 : EZ - 1;
+      const int r = h % zf;
+      ex = r % EX;
+      ey = r / EX;
+    } else if (h < 2 * (zf + yf)) {
+      const int h2 = h - 2 * zf;
+      ey = h2 < yf ? 0 : EY - 1;
+      const int r = h2 % yf;
+      ex = r % EX;
+      ez = 1 + r / EX;
+    } else {
+      const int h3 = h - 2 * (zf + yf);
+      ex = h3 < xf ? 0 : EX - 1;
+      const int r = h3 % xf;
+      ey = 1 + r % BY;
+      ez = 1 + r / BY;
+    }
+    e = ex + EX * (ey + EY * ez);
+    gi = i0 - 1 + ex;
+    gj = j0 - 1 + ey;
+    gk = k0 - 1 + ez;
+  };
+  auto interior = [&](int gi, int gj, int gk) {
+    return gi > 0 && gi < g.nx && gj > 0 && gj < g.ny && gk > 0 && gk < g.nz;
+  };
+  // ---- start: r_0 on the box and its halo, x; p = s = 0; w_0 = A r_0; publish w_0, s = 0
+  for (int e = threadIdx.x; e < ext; e += kRsThreads) R[e] = 0.0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < B; q += kRsThreads) {
+    const Own w = own_node(q);
+    R[w.e] = w.valid ? D.r[w.o] : 0.0;
+    X[q] = w.valid ? D.x[w.o] : 0.0;
+    P[q] = 0.0;
+    Sv[q] = 0.0;
+  }
+  for (int h = threadIdx.x; h < nshell; h += kRsThreads) {
+    int e, gi, gj, gk;
+    shell_node(h, e, gi, gj, gk);
+    R[e] = interior(gi, gj, gk) ? D.r[gi + gj * g.sy + (long long)gk * g.sz] : 0.0;
+  }
+  __syncthreads();
+  double acc_d = 0.0;
+  for (int q = threadIdx.x; q < B; q += kRsThreads) {
+    const Own n = own_node(q);
+    double w = 0.0;
+    if (n.valid) {
+      w = rs_stencil(R + n.e, EX, EX * EY, A);
+      acc_d = fma(w, R[n.e], acc_d);
+      D.w0[n.o] = w;
+      D.s0[n.o] = 0.0;
+    }
+    W[q] = w;
+  }
+  double gam = S->rr, alpha = 0.0, beta = 0.0, delta = 0.0;
+  const double tol2 = S->tol2;
+  int iter = S->iter;
+  const int max_iter = S->max_iter, fixed = S->fixed;
+  int status = EXCMG_OK;
+  unsigned seq = 1;
+  if (!rs_grid_sum2(0.0, acc_d, pairs, counter, G, seq++, err, s_warp, &s_red, &s_ok)) {
+    status = EXCMG_ERR_TIMEOUT;
+    s_stop = 1;
+  } else if (threadIdx.x == 0) {
+    delta = s_red.y;
+    int stop = 0;
+    if (delta == 0.0 && gam == 0.0) {
+      stop = 1;  // exact solution (fixed-count mode)
+    } else if (!(delta > 0.0) || !isfinite(delta)) {
+      status = EXCMG_ERR_NONFINITE;
+      stop = 1;
+    } else {
+      alpha = gam / delta;
+    }
+    s_stop = stop;
+    s_alpha = alpha;
+    s_beta = 0.0;
+  }
+  __syncthreads();
+  int par = 0;  // step i reads the published r_i, w_i, s_{i-1} of parity par
+  while (!s_stop) {
+    const double a = s_alpha, bt = s_beta;
+    const double* Rg = par ? D.r1 : D.r;
+    const double* Wg = par ? D.w1 : D.w0;
+    const double* Sg = par ? D.s1 : D.s0;
+    double* Rn = par ? D.r : D.r1;
+    double* Wn = par ? D.w0 : D.w1;
+    double* Sn = par ? D.s0 : D.s1;
+    // 1. the halo's published r, w, s: the loads of up to kRsHB shell nodes per thread
+    // are issued first, so that their latency overlaps the own-node update
+    double hr[kRsHB], hw[kRsHB], hs[kRsHB];
+    int he[kRsHB];
+#pragma unroll
+    for (int u = 0; u < kRsHB; ++u) {
+      const int h = threadIdx.x + u * kRsThreads;
+      he[u] = -1;
+      hr[u] = hw[u] = hs[u] = 0.0;
+      if (h < nshell) {
+        int gi, gj, gk;
+        shell_node(h, he[u], gi, gj, gk);
+        if (interior(gi, gj, gk)) {
+          const long long o = gi + gj * g.sy + (long long)gk * g.sz;
+          hr[u] = __ldcg(Rg + o);
+          hw[u] = __ldcg(Wg + o);
+          hs[u] = __ldcg(Sg + o);
+        }
+      }
+    }
+    // 2. own nodes: p, s, x, r; publish r and s
+    for (int q = threadIdx.x; q < B; q += kRsThreads) {
+      const Own n = own_node(q);
+      if (!n.valid) continue;
+      const int e = n.e;
+      const long long o = n.o;
+      const double r = R[e];
+      const double pv = fma(bt, P[q], r);
+      const double sv = fma(bt, Sv[q], W[q]);
+      P[q] = pv;
+      Sv[q] = sv;
+      X[q] = fma(a, pv, X[q]);
+      const double rn = fma(-a, sv, r);
+      R[e] = rn;
+      __stcg(Rn + o, rn);
+      __stcg(Sn + o, sv);
+    }
+    // 3. the halo's new r, with the owner's fused operations (zero on the boundary: the
+    // loads above left r = w = s = 0 there); shells larger than kRsHB per thread finish
+    // with plain loads
+#pragma unroll
+    for (int u = 0; u < kRsHB; ++u)
+      if (he[u] >= 0) R[he[u]] = fma(-a, fma(bt, hs[u], hw[u]), hr[u]);
+    for (int h = threadIdx.x + kRsHB * kRsThreads; h < nshell; h += kRsThreads) {
+      int e, gi, gj, gk;
+      shell_node(h, e, gi, gj, gk);
+      double rn = 0.0;
+      if (interior(gi, gj, gk)) {
+        const long long o = gi + gj * g.sy + (long long)gk * g.sz;
+        rn = fma(-a, fma(bt, __ldcg(Sg + o), __ldcg(Wg + o)), __ldcg(Rg + o));
+      }
+      R[e] = rn;
+    }
+    __syncthreads();
+    // 4. w = A r, gamma, delta; publish w
+    double acc_g = 0.0;
+    acc_d = 0.0;
+    for (int q = threadIdx.x; q < B; q += kRsThreads) {
+      const Own n = own_node(q);
+      double w = 0.0;
+      if (n.valid) {
+        const double r = R[n.e];
+        w = rs_stencil(R + n.e, EX, EX * EY, A);
+        acc_g = fma(r, r, acc_g);
+        acc_d = fma(w, r, acc_d);
+        __stcg(Wn + n.o, w);
+      }
+      W[q] = w;
+    }
+    // 5. the grid reduction (it also orders every block's publications before the next
+    // step's halo loads), scalars
+    const bool ok = rs_grid_sum2(acc_g, acc_d, pairs, counter, G, seq++, err, s_warp, &s_red, &s_ok);
+    if (threadIdx.x == 0) {
+      int stop = 0;
+      if (!ok) {
+        status = EXCMG_ERR_TIMEOUT;
+        stop = 1;
+      } else {
+        const double gn = s_red.x, dn = s_red.y;
+        iter += 1;
+        if (!isfinite(gn) || !isfinite(dn)) {
+          status = EXCMG_ERR_NONFINITE;
+          stop = 1;
+        } else if (gn <= tol2 || gn == 0.0) {
+          stop = 1;  // converged (or exact solution in fixed-count mode)
+        } else if (iter >= max_iter) {
+          if (!fixed) status = EXCMG_ERR_NOT_CONVERGED;
+          stop = 1;
+        } else {
+          // alpha' = gn / (dn - beta' gn / alpha) = gn k / (dn k - gn^2), k = gam alpha
+          const double k = gam * alpha;
+          const double den = fma(dn, k, -gn * gn);
+          if (!(den > 0.0)) {
+            status = EXCMG_ERR_NONFINITE;
+            stop = 1;
+          } else {
+            alpha = gn * k / den;
+            beta = gn / gam;
+          }
+        }
+        gam = gn;
+        delta = dn;
+      }
+      s_stop = stop;
+      s_alpha = alpha;
+      s_beta = beta;
+    }
+    __syncthreads();
+    par ^= 1;
+  }
+  // x and the last r of the box
+  for (int q = threadIdx.x; q < B; q += kRsThreads) {
+    const Own n = own_node(q);
+    if (!n.valid) continue;
+    D.x[n.o] = X[q];
+    D.r[n.o] = R[n.e];
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    S->rr = gam;
+    S->pq = delta;
+    S->alpha = alpha;
+    S->beta = beta;
+    S->iter = iter;
+    S->first = 0;
+    S->status = status;
+    S->done = 1;
+  }
+}
+
+int g_rs_blocks_per_sm = 0;  // at the largest shared memory a box may take
+int g_rs_sms = 0;
+size_t g_rs_max_smem = 0;
+
+}  // namespace
+
+size_t resident_smem(int bx, int by, int bz) {
+  const size_t ext = (size_t)(bx + 2) * (by + 2) * (bz + 2);
+  return sizeof(double) * (ext + 4 * (size_t)bx * by * bz);
+}
+
+#ifndef EXCMG_RESIDENT_MAX_SMEM
+#define EXCMG_RESIDENT_MAX_SMEM (96 * 1024)
+#endif
+
+bool resident_box(const Grid3& g, ResidentDesc& D, size_t& smem) {
+  if (g_rs_sms == 0) {
+    int dev = 0, coop = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&g_rs_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    g_rs_max_smem = std::min<size_t>(EXCMG_RESIDENT_MAX_SMEM, (size_t)std::max(0, optin - 2048));
+    if (!coop || g_rs_sms <= 0 ||
+        cudaFuncSetAttribute(k_cg_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)g_rs_max_smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_rs_blocks_per_sm, k_cg_resident, kRsThreads,
+                                                      g_rs_max_smem) != cudaSuccess) {
+      cudaGetLastError();
+      g_rs_blocks_per_sm = 0;
+    }
+    if (g_rs_sms <= 0) g_rs_sms = 1;
+  }
+  if (g_rs_blocks_per_sm <= 0) return false;
+  const int ni = g.nx - 1, nj = g.ny - 1, nk = g.nz - 1;
+  if (ni < 1 || nj < 1 || nk < 1) return false;
+  const long long max_blocks = std::min<long long>((long long)g_rs_sms * g_rs_blocks_per_sm, kMaxGrid);
+  // per-step model in SM clocks: the busiest SM's float64 work (~12.5 clocks per node,
+  // 2 DFMA per clock) plus the halo loads of a box (3 per shell node)
+  double best = 1e300;
+  bool found = false;
+  const int bxs[] = {32, 16, 8};
+  const int bys[] = {1, 2, 4, 8, 16, 32};
+  const int bzs[] = {1, 2, 4, 8, 16, 32};
+  for (int bx : bxs)
+    for (int by : bys)
+      for (int bz : bzs) {
+        const long long nb = (long long)((ni + bx - 1) / bx) * ((nj + by - 1) / by) * ((nk + bz - 1) / bz);
+        if (nb > max_blocks) continue;
+        const size_t sm = resident_smem(bx, by, bz);
+        if (sm > g_rs_max_smem) continue;
+        const double B = (double)bx * by * bz;
+        const double shell = (double)(bx + 2) * (by + 2) * (bz + 2) - B;
+        const double per_sm = (double)((nb + g_rs_sms - 1) / g_rs_sms);
+        const double cost = per_sm * B * 12.5 + shell * 6.0;
+        if (cost < best) {
+          best = cost;
+          found = true;
+          D.bx = bx;
+          D.by = by;
+          D.bz = bz;
+          D.nbx = (ni + bx - 1) / bx;
+          D.nby = (nj + by - 1) / by;
+          D.nbz = (nk + bz - 1) / bz;
+          smem = sm;
+        }
+      }
+  return found;
+}
+
+cudaError_t launch_cg_resident(const ResidentDesc& D, size_t smem, CGState* st, double2* pairs,
+                               unsigned* counter, int* err, cudaStream_t s) {
+  const int grid = D.nbx * D.nby * D.nbz;
+  ResidentDesc d = D;
+  void* args[] = {(void*)&d, (void*)&st, (void*)&pairs, (void*)&counter, (void*)&err};
+  return cudaLaunchCooperativeKernel((const void*)k_cg_resident, dim3(grid), dim3(kRsThreads), args,
+                                     smem, s);
+}
+
+}  // namespace excmg

@@ -5,17 +5,23 @@
 //
 // EXP_finite works on bricks of 32 x 8 x 8 fine cells (four interpolation cells along x,
 // each cell = 2x2x2 elements of grid 4h = 8 fine cells per direction).  Per brick:
-//  1. stage the 17x5x5 nodes of grid 2h and the 9x3x3 nodes of grid 4h in shared memory;
-//  2. w at every node of grid 2h: u_2h + (1/16) * (mean of d = u_2h - u_4h over the
+//  1. w at every node of grid 2h: u_2h + (1/16) * (mean of d = u_2h - u_4h over the
 //     grid-4h corners of the edge / face / element it is the centre of; d itself at a
 //     grid-4h node).  This is eq. (jiedian) at corners ((17u1 - u0)/16 = u1 + d/16),
 //     eq. (zhongdian) at edge midpoints (u1 + (d_a + d_b)/32), and the arithmetic means
-//     of eq. (zhongdian) over the two face diagonals / four space diagonals;
-//  3. tri-quartic interpolation (eq. inter) as three one-dimensional quartic passes
-//     (x, then y, then z) with the Lagrange weights at the quarter points: the tensor
-//     product l_i(xi) l_j(eta) l_k(zeta) applied by sum factorisation, ~6 FMA per node
-//     instead of the 125 of the 604x125 matrix form.
+//     of eq. (zhongdian) over the two face diagonals / four space diagonals.  The corner
+//     sums are formed separably (x, then y, then z: one add per odd coordinate) and the
+//     power-of-two factor 1/(16 * 2^(number of odd coordinates)) is applied in one FMA;
+//  2. tri-quartic interpolation (eq. inter) as three one-dimensional quartic passes
+//     (x, then y, then z) with the Lagrange weights at the half-integer points of a cell:
+//     the tensor product l_i(xi) l_j(eta) l_k(zeta) applied by sum factorisation, ~6 FMA
+//     per node instead of the 125 of the 604x125 matrix form.
+// Every pass splits its outputs by parity (copies at even positions, arithmetic at odd
+// ones) so that the float64 work of a warp runs with all lanes active: on GB300 a warp
+// instruction on the narrow FP64 pipe costs the same whether 16 or 32 lanes need it.
 #include <math.h>
+
+#include <algorithm>
 
 #include "excmg_internal.cuh"
 
@@ -37,119 +43,138 @@ constexpr int BX0 = 9, BY0 = 3, BZ0 = 3;   // grid-4h nodes of a brick
 constexpr int BXF = 33, BYF = 9, BZF = 9;  // fine nodes of a brick
 
 struct BrickSmem {
-  double u1[BZ1][BY1][BX1];
-  double d[BZ0][BY0][BX0];
-  double w[BZ1][BY1][BX1];
-  double x[BZ1][BY1][BXF];
-  double y[BZ1][BYF][BXF];
+  double wq[4][5];            // c_wq, indexed per lane
+  double u1[BZ1][BY1][BX1];   // grid-2h values
+  double tx[BZ0][BY0][BX1];   // corner sums of d along x (grid-4h rows, grid-2h columns)
+  double ty[BZ0][BY1][BX1];   // ... then along y
+  double w[BZ1][BY1][BX1];    // extrapolated values at the grid-2h nodes
+  double x[BZ1][BY1][BXF];    // after the quartic pass along x
+  double y[BZ1][BYF][BXF];    // after the quartic pass along y
 };
 
 // One brick (local index lb) of EXP_finite for descriptor d.
 __device__ void exp_finite_brick(const ProlongDesc& d, long long lb, BrickSmem& S) {
-  auto& s_u1 = S.u1;
-  auto& s_d = S.d;
-  auto& s_w = S.w;
-  auto& s_x = S.x;
-  auto& s_y = S.y;
-  {
-    const Grid3 g = d.g;
-    const int bx = (int)(lb % d.nbx);
-    const int by = (int)((lb / d.nbx) % d.nby);
-    const int bz = (int)(lb / ((long long)d.nbx * d.nby));
-    const int n1x = g.nx / 2, n1y = g.ny / 2, n1z = g.nz / 2;
-    const int n0x = g.nx / 4, n0y = g.ny / 4, n0z = g.nz / 4;
-    const long long s1y = n1x + 1, s1z = (long long)(n1x + 1) * (n1y + 1);
-    const long long s0y = n0x + 1, s0z = (long long)(n0x + 1) * (n0y + 1);
-    __syncthreads();  // shared buffers of the previous brick are free
-    // 1. stage grid-2h and grid-4h values
-    for (int idx = threadIdx.x; idx < BZ1 * BY1 * BX1; idx += kThreads) {
-      const int ix = idx % BX1, jy = (idx / BX1) % BY1, kz = idx / (BX1 * BY1);
-      const int I = 16 * bx + ix, J = 4 * by + jy, K = 4 * bz + kz;
-      s_u1[kz][jy][ix] = (I <= n1x && J <= n1y && K <= n1z) ? d.u2h[I + J * s1y + K * s1z] : 0.0;
-    }
-    for (int idx = threadIdx.x; idx < BZ0 * BY0 * BX0; idx += kThreads) {
-      const int ix = idx % BX0, jy = (idx / BX0) % BY0, kz = idx / (BX0 * BY0);
-      const int I = 8 * bx + ix, J = 2 * by + jy, K = 2 * bz + kz;
-      s_d[kz][jy][ix] = (I <= n0x && J <= n0y && K <= n0z) ? d.u4h[I + J * s0y + K * s0z] : 0.0;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < BZ0 * BY0 * BX0; idx += kThreads) {
-      const int ix = idx % BX0, jy = (idx / BX0) % BY0, kz = idx / (BX0 * BY0);
-      s_d[kz][jy][ix] = s_u1[2 * kz][2 * jy][2 * ix] - s_d[kz][jy][ix];
-    }
-    __syncthreads();
-    // 2. extrapolated values at the grid-2h nodes
-    for (int idx = threadIdx.x; idx < BZ1 * BY1 * BX1; idx += kThreads) {
-      const int ix = idx % BX1, jy = (idx / BX1) % BY1, kz = idx / (BX1 * BY1);
-      const int ox = ix & 1, oy = jy & 1, oz = kz & 1;
-      const int cx = ix >> 1, cy = jy >> 1, cz = kz >> 1;
-      double sum = 0.0;
-      for (int a = 0; a <= oz; ++a)
-        for (int bb = 0; bb <= oy; ++bb)
-          for (int c = 0; c <= ox; ++c) sum += s_d[cz + a][cy + bb][cx + c];
-      // (1/16) * mean over 2^(ox+oy+oz) corners: a power-of-two scale, exact as a product
-      const double scale = 0.0625 / (double)(1 << (ox + oy + oz));
-      s_w[kz][jy][ix] = fma(sum, scale, s_u1[kz][jy][ix]);
-    }
-    __syncthreads();
-    // 3a. quartic along x
-    for (int idx = threadIdx.x; idx < BZ1 * BY1 * BXF; idx += kThreads) {
-      const int lx = idx % BXF, jy = (idx / BXF) % BY1, kz = idx / (BXF * BY1);
-      double v;
-      if ((lx & 1) == 0) {
-        v = s_w[kz][jy][lx >> 1];
-      } else {
-        const int I = (lx - 1) >> 1, base = (I >> 2) << 2, t = I & 3;
-        v = 0.0;
+  const Grid3 g = d.g;
+  const int bx = (int)(lb % d.nbx);
+  const int by = (int)((lb / d.nbx) % d.nby);
+  const int bz = (int)(lb / ((long long)d.nbx * d.nby));
+  const int n1x = g.nx / 2, n1y = g.ny / 2, n1z = g.nz / 2;
+  const int n0x = g.nx / 4, n0y = g.ny / 4, n0z = g.nz / 4;
+  const long long s1y = n1x + 1, s1z = (long long)(n1x + 1) * (n1y + 1);
+  const long long s0y = n0x + 1, s0z = (long long)(n0x + 1) * (n0y + 1);
+  // d = u_2h - u_4h at grid-4h node (I, J, K) of the level (0 outside the grid)
+  auto dval = [&](int I, int J, int K) -> double {
+    if (I > n0x || J > n0y || K > n0z) return 0.0;
+    return d.u2h[2 * I + 2 * J * s1y + 2 * K * s1z] - d.u4h[I + J * s0y + K * s0z];
+  };
+  __syncthreads();  // shared buffers of the previous brick are free
+  // 1a. stage grid-2h values; corner sums of d along x (even columns: d, odd: d_a + d_b)
+  for (int idx = threadIdx.x; idx < BZ1 * BY1 * BX1; idx += kThreads) {
+    const int ix = idx % BX1, jy = (idx / BX1) % BY1, kz = idx / (BX1 * BY1);
+    const int I = 16 * bx + ix, J = 4 * by + jy, K = 4 * bz + kz;
+    S.u1[kz][jy][ix] = (I <= n1x && J <= n1y && K <= n1z) ? d.u2h[I + J * s1y + K * s1z] : 0.0;
+  }
+  for (int idx = threadIdx.x; idx < BZ0 * BY0 * BX0; idx += kThreads) {
+    const int i0 = idx % BX0, j0 = (idx / BX0) % BY0, k0 = idx / (BX0 * BY0);
+    S.tx[k0][j0][2 * i0] = dval(8 * bx + i0, 2 * by + j0, 2 * bz + k0);
+  }
+  for (int idx = threadIdx.x; idx < BZ0 * BY0 * (BX0 - 1); idx += kThreads) {
+    const int i0 = idx % (BX0 - 1), j0 = (idx / (BX0 - 1)) % BY0, k0 = idx / ((BX0 - 1) * BY0);
+    const int I = 8 * bx + i0, J = 2 * by + j0, K = 2 * bz + k0;
+    S.tx[k0][j0][2 * i0 + 1] = dval(I, J, K) + dval(I + 1, J, K);
+  }
+  __syncthreads();
+  // 1b. along y
+  for (int idx = threadIdx.x; idx < BZ0 * BY0 * BX1; idx += kThreads) {
+    const int ix = idx % BX1, j0 = (idx / BX1) % BY0, k0 = idx / (BX1 * BY0);
+    S.ty[k0][2 * j0][ix] = S.tx[k0][j0][ix];
+  }
+  for (int idx = threadIdx.x; idx < BZ0 * (BY0 - 1) * BX1; idx += kThreads) {
+    const int ix = idx % BX1, j0 = (idx / BX1) % (BY0 - 1), k0 = idx / (BX1 * (BY0 - 1));
+    S.ty[k0][2 * j0 + 1][ix] = S.tx[k0][j0][ix] + S.tx[k0][j0 + 1][ix];
+  }
+  __syncthreads();
+  // 1c. along z, and w = u_2h + sum / (16 * 2^(odd coordinates)) (a power of two: exact)
+  for (int idx = threadIdx.x; idx < BZ0 * BY1 * BX1; idx += kThreads) {
+    const int ix = idx % BX1, jy = (idx / BX1) % BY1, k0 = idx / (BX1 * BY1);
+    const double scale = 0.0625 / (double)(1 << ((ix & 1) + (jy & 1)));
+    S.w[2 * k0][jy][ix] = fma(S.ty[k0][jy][ix], scale, S.u1[2 * k0][jy][ix]);
+  }
+  for (int idx = threadIdx.x; idx < (BZ0 - 1) * BY1 * BX1; idx += kThreads) {
+    const int ix = idx % BX1, jy = (idx / BX1) % BY1, k0 = idx / (BX1 * BY1);
+    const double scale = 0.03125 / (double)(1 << ((ix & 1) + (jy & 1)));
+    S.w[2 * k0 + 1][jy][ix] = fma(S.ty[k0][jy][ix] + S.ty[k0 + 1][jy][ix], scale, S.u1[2 * k0 + 1][jy][ix]);
+  }
+  __syncthreads();
+  // 2a. quartic along x: even fine columns are grid-2h columns
+  for (int idx = threadIdx.x; idx < BZ1 * BY1 * BX1; idx += kThreads) {
+    const int ix = idx % BX1, jy = (idx / BX1) % BY1, kz = idx / (BX1 * BY1);
+    S.x[kz][jy][2 * ix] = S.w[kz][jy][ix];
+  }
+  for (int idx = threadIdx.x; idx < BZ1 * BY1 * (BX1 - 1); idx += kThreads) {
+    const int I = idx % (BX1 - 1), jy = (idx / (BX1 - 1)) % BY1, kz = idx / ((BX1 - 1) * BY1);
+    const int t = I & 3, base = I - t;
+    double v = 0.0;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) v = fma(c_wq[t][m], s_w[kz][jy][base + m], v);
-      }
-      s_x[kz][jy][lx] = v;
-    }
-    __syncthreads();
-    // 3b. quartic along y
-    for (int idx = threadIdx.x; idx < BZ1 * BYF * BXF; idx += kThreads) {
-      const int lx = idx % BXF, ly = (idx / BXF) % BYF, kz = idx / (BXF * BYF);
-      double v;
-      if ((ly & 1) == 0) {
-        v = s_x[kz][ly >> 1][lx];
-      } else {
-        const int t = (ly - 1) >> 1;
-        v = 0.0;
+    for (int m = 0; m < 5; ++m) v = fma(S.wq[t][m], S.w[kz][jy][base + m], v);
+    S.x[kz][jy][2 * I + 1] = v;
+  }
+  __syncthreads();
+  // 2b. quartic along y
+  for (int idx = threadIdx.x; idx < BZ1 * BY1 * BXF; idx += kThreads) {
+    const int lx = idx % BXF, jy = (idx / BXF) % BY1, kz = idx / (BXF * BY1);
+    S.y[kz][2 * jy][lx] = S.x[kz][jy][lx];
+  }
+  for (int idx = threadIdx.x; idx < BZ1 * (BY1 - 1) * BXF; idx += kThreads) {
+    const int lx = idx % BXF, t = (idx / BXF) % (BY1 - 1), kz = idx / (BXF * (BY1 - 1));
+    double v = 0.0;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) v = fma(c_wq[t][m], s_x[kz][m][lx], v);
-      }
-      s_y[kz][ly][lx] = v;
-    }
-    __syncthreads();
-    // 3c. quartic along z, boundary data, store
+    for (int m = 0; m < 5; ++m) v = fma(S.wq[t][m], S.x[kz][m][lx], v);
+    S.y[kz][2 * t + 1][lx] = v;
+  }
+  __syncthreads();
+  // 2c. quartic along z, boundary data, store.  Main part: the 32 x 8 x 8 nodes whose
+  // brick-local coordinates are all below the brick's far faces -- one fine plane per
+  // pass of the block, one row of 32 nodes per warp (uniform parity, coalesced stores).
+  const bool has_g = d.gb.p != nullptr;
+  auto value = [&](int lx, int ly, int lz, int gx, int gy, int gz) -> double {
+    const bool bnd = gx == 0 || gx == g.nx || gy == 0 || gy == g.ny || gz == 0 || gz == g.nz;
+    if (bnd && has_g) return d.gb.at(gx, gy, gz);
+    if ((lz & 1) == 0) return S.y[lz >> 1][ly][lx];
+    const int t = (lz - 1) >> 1;
+    double v = 0.0;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) v = fma(S.wq[t][m], S.y[m][ly][lx], v);
+    return v;
+  };
+  for (int idx = threadIdx.x; idx < 32 * 8 * 8; idx += kThreads) {
+    const int lx = idx & 31, ly = (idx >> 5) & 7, lz = idx >> 8;
+    const int gx = 32 * bx + lx, gy = 8 * by + ly, gz = 8 * bz + lz;
+    if (gx > g.nx || gy > g.ny || gz > g.nz) continue;
+    d.w[gx + gy * g.sy + (long long)gz * g.sz] = value(lx, ly, lz, gx, gy, gz);
+  }
+  // far faces of the brick that lie on the far faces of the grid (no next brick owns them)
+  const bool xe = 32 * bx + 32 == g.nx, ye = 8 * by + 8 == g.ny, ze = 8 * bz + 8 == g.nz;
+  if (xe || ye || ze) {
     for (int idx = threadIdx.x; idx < BZF * BYF * BXF; idx += kThreads) {
       const int lx = idx % BXF, ly = (idx / BXF) % BYF, lz = idx / (BXF * BYF);
+      const bool far = (lx == 32) || (ly == 8) || (lz == 8);
+      if (!far || (lx == 32 && !xe) || (ly == 8 && !ye) || (lz == 8 && !ze)) continue;
       const int gx = 32 * bx + lx, gy = 8 * by + ly, gz = 8 * bz + lz;
       if (gx > g.nx || gy > g.ny || gz > g.nz) continue;
-      if ((lx == BXF - 1 && gx != g.nx) || (ly == BYF - 1 && gy != g.ny) ||
-          (lz == BZF - 1 && gz != g.nz))
-        continue;  // owned by the next brick
-      double v;
-      const bool bnd = gx == 0 || gx == g.nx || gy == 0 || gy == g.ny || gz == 0 || gz == g.nz;
-      if (bnd && d.gb.p != nullptr) {
-        v = d.gb.at(gx, gy, gz);
-      } else if ((lz & 1) == 0) {
-        v = s_y[lz >> 1][ly][lx];
-      } else {
-        const int t = (lz - 1) >> 1;
-        v = 0.0;
-#pragma unroll
-        for (int m = 0; m < 5; ++m) v = fma(c_wq[t][m], s_y[m][ly][lx], v);
-      }
-      d.w[gx + gy * g.sy + (long long)gz * g.sz] = v;
+      d.w[gx + gy * g.sy + (long long)gz * g.sz] = value(lx, ly, lz, gx, gy, gz);
     }
   }
+}
+
+__device__ __forceinline__ void load_weights(BrickSmem& S) {
+  if (threadIdx.x < 20) S.wq[threadIdx.x / 5][threadIdx.x % 5] = c_wq[threadIdx.x / 5][threadIdx.x % 5];
 }
 
 __global__ void __launch_bounds__(kThreads)
     k_exp_finite(int nprob, const ProlongDesc* __restrict__ descs, long long total_blocks) {
   __shared__ BrickSmem S;
+  load_weights(S);
   int p = 0;
   for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) {
     while (p + 1 < nprob && b >= descs[p + 1].block_begin) ++p;
@@ -159,6 +184,7 @@ __global__ void __launch_bounds__(kThreads)
 
 __global__ void __launch_bounds__(kThreads) k_exp_finite_one(ProlongDesc d, long long total_blocks) {
   __shared__ BrickSmem S;
+  load_weights(S);
   for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) exp_finite_brick(d, b, S);
 }
 
@@ -247,18 +273,31 @@ int flat_grid(long long n) {
 
 }  // namespace
 
+// Co-resident blocks of an EXP_finite kernel on the whole device (one full wave).
+static int brick_wave(const void* kernel, int& cache) {
+  if (cache == 0) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0);
+    cache = std::max(1, sms) * std::max(1, occ);
+  }
+  return cache;
+}
+static int g_wave_many = 0, g_wave_one = 0;
+
 cudaError_t launch_exp_finite(int nprob, const ProlongDesc* descs, long long total_blocks,
                               cudaStream_t s) {
-  long long grid = total_blocks < 152 * 8 ? total_blocks : 152 * 8;
-  if (grid < 1) grid = 1;
+  const long long wave = brick_wave((const void*)k_exp_finite, g_wave_many);
+  const long long grid = std::max(1LL, std::min(total_blocks, wave));
   k_exp_finite<<<(int)grid, kThreads, 0, s>>>(nprob, descs, total_blocks);
   return cudaGetLastError();
 }
 
 cudaError_t launch_exp_finite_one(const ProlongDesc& d, cudaStream_t s) {
   const long long total = (long long)d.nbx * d.nby * d.nbz;
-  long long grid = total < 152 * 8 ? total : 152 * 8;
-  if (grid < 1) grid = 1;
+  const long long wave = brick_wave((const void*)k_exp_finite_one, g_wave_one);
+  const long long grid = std::max(1LL, std::min(total, wave));
   k_exp_finite_one<<<(int)grid, kThreads, 0, s>>>(d, total);
   return cudaGetLastError();
 }

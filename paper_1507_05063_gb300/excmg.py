@@ -26,7 +26,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 MAX_LEVELS = 24
 FP64, MIXED = 0, 1
 KERNEL_NAMES = ["spmv_f64", "update_f64", "spmv_f32", "update_f32", "residual", "exp_finite",
-                "init", "correct", "exp_true", "cg_f64", "cg_f32", "cg_small_f64", "cg_small_f32"]
+                "init", "correct", "exp_true", "cg_f64", "cg_f32", "cg_cluster_f64", "cg_cluster_f32",
+                "cg_resident_f64"]
 KERNEL_KINDS = len(KERNEL_NAMES)
 STATUS = {0: "EXCMG_OK", 1: "EXCMG_ERR_INVALID_ARG", 2: "EXCMG_ERR_NOT_CONVERGED",
           3: "EXCMG_ERR_CUDA", 4: "EXCMG_ERR_NONFINITE", 5: "EXCMG_ERR_TIMEOUT",

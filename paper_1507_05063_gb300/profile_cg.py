@@ -1,7 +1,8 @@
-"""Runs one finest-grid CG solve with a fixed number of steps, for profilers.
+"""Runs one finest-grid CG solve with a fixed number of steps (or one residual or one
+EXP_finite launch on that grid), for profilers.
 
     python -m paper_1507_05063_gb300.profile_cg [--N 512 256 128] [--steps 20]
-        [--precision fp64|mixed] [--repeat 1]
+        [--precision fp64|mixed] [--repeat 1] [--op cg|residual|exp_finite]
 
 The problem is u = exp(x+y+z) on [0,1]^3 (f = 3u, g = u); CG starts from zero in the
 interior.  The solve goes through excmg_cg (FP64: one k_cg_persistent<double> launch for
@@ -27,12 +28,31 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--op", default="cg", choices=["cg", "residual", "exp_finite"])
     a = ap.parse_args()
     N, L = tuple(a.N), (1.0, 1.0, 1.0)
     f, g, _ = P.make_inputs(P.PROBLEMS["exp3"], N)
     fd = torch.from_numpy(f).cuda()
     start = g.copy()
     start[1:-1, 1:-1, 1:-1] = 0.0
+    if a.op != "cg":
+        # residual of the zero-interior start; EXP_finite from the exact solution sampled on
+        # the grids with N/2 and N/4 cells
+        u0 = torch.from_numpy(start).cuda()
+        u2 = torch.from_numpy(P.make_inputs(P.PROBLEMS["exp3"], tuple(n // 2 for n in N))[2]).cuda()
+        u4 = torch.from_numpy(P.make_inputs(P.PROBLEMS["exp3"], tuple(n // 4 for n in N))[2]).cuda()
+        for _ in range(a.repeat):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if a.op == "residual":
+                out, rn, bn = X.residual(fd, u0, L)
+            else:
+                out = X.exp_finite(u2, u4, L)
+            e1.record()
+            torch.cuda.synchronize()
+            print(f"N={N} {a.op} ms={e0.elapsed_time(e1):.3f}", flush=True)
+        assert np.isfinite(out.cpu().numpy()).all()
+        return
     for _ in range(a.repeat):
         u = torch.from_numpy(start).cuda()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
