@@ -79,6 +79,10 @@ ALGO = {
     # all CG steps of a mid-size grid, vectors resident in the blocks' shared memory: the
     # same 25 operations; global traffic = the published r, s, w of every node (24 B)
     "cg_resident_f64": {"bytes": 24.0, "dp_ops": 25.0},
+    # DSOLVE by the sine transform: b in, x and the check residual out; per unknown
+    # 2 (mx + my + mz) FMA for the transforms (~25 on the workloads' 16x8x4 grid), the
+    # division, and the 19-point check
+    "dsolve": {"bytes": 24.0, "dp_ops": 72.0},
 }
 KERNEL_SYMBOL = {"spmv_f64": "k_dir_spmv_dot<double>", "update_f64": "k_update_dot<double>",
                  "spmv_f32": "k_dir_spmv_dot<float>", "update_f32": "k_update_dot<float>",
@@ -86,14 +90,15 @@ KERNEL_SYMBOL = {"spmv_f64": "k_dir_spmv_dot<double>", "update_f64": "k_update_d
                  "correct": "k_add_correction", "exp_true": "k_exp_true",
                  "cg_f64": "k_cg_persistent<double>", "cg_f32": "k_cg_persistent<float>",
                  "cg_cluster_f64": "k_cg_cluster<double>", "cg_cluster_f32": "k_cg_cluster<float>",
-                 "cg_resident_f64": "k_cg_resident"}
+                 "cg_resident_f64": "k_cg_resident", "dsolve": "k_dsolve"}
 KERNEL_SOURCE = {"spmv_f64": "cg_kernels.cu", "update_f64": "cg_kernels.cu",
                  "spmv_f32": "cg_kernels.cu", "update_f32": "cg_kernels.cu",
                  "residual": "cg_kernels.cu", "exp_finite": "transfer_kernels.cu",
                  "init": "transfer_kernels.cu", "correct": "cg_kernels.cu",
                  "exp_true": "transfer_kernels.cu", "cg_f64": "cg_kernels.cu",
                  "cg_f32": "cg_kernels.cu", "cg_cluster_f64": "cluster_cg.cu",
-                 "cg_cluster_f32": "cluster_cg.cu", "cg_resident_f64": "resident_cg.cu"}
+                 "cg_cluster_f32": "cluster_cg.cu", "cg_resident_f64": "resident_cg.cu",
+                 "dsolve": "dsolve_kernels.cu"}
 # FP64 issue rate: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz (maximum SM clock).
 DP_PEAK_GOPS = 2 * 152 * 2.070
 
@@ -189,7 +194,7 @@ def oracle_solve_seconds(wl, f, g):
     import oracle as O
     name, L, N, N0, eps, epsc = WORKLOADS[wl]
     t0 = time.perf_counter()
-    res = O.excmg(f, g, L, N, N0, eps=eps, eps_coarse=epsc, want_utilde=False)
+    res = O.excmg(f, g, L, N, N0, eps=eps, eps_coarse=epsc, dsolve="dense", want_utilde=False)
     return time.perf_counter() - t0, res
 
 

@@ -72,7 +72,8 @@ typedef enum {
   EXCMG_K_CG_CLUSTER_F32 = 12, /* the same in float32 */
   EXCMG_K_CG_RESIDENT_F64 = 13, /* all CG steps of a mid-size grid, vectors resident in the
                                    blocks' shared memory (float64) */
-  EXCMG_KERNEL_KINDS = 14
+  EXCMG_K_DSOLVE = 14,    /* direct solve of a coarse level (discrete sine transform) */
+  EXCMG_KERNEL_KINDS = 15
 } excmg_kernel_kind;
 
 /* Box and grids (Section 2: hx = Lx/Nx ...; Algorithm 1: coarsest grid H, L levels). */
@@ -88,7 +89,7 @@ typedef struct {
   double eps;              /* relative-residual tolerance on levels >= 2: CG stops when
                               ||A u - b||_2 <= eps ||b||_2, b the assembled right-hand
                               side with its Dirichlet lift (Algorithm 1, line 7) */
-  double eps_coarse;       /* same test on levels 0 and 1 (stands in for DSOLVE) */
+  double eps_coarse;       /* same test on levels 0 and 1 when DSOLVE is CG */
   int max_iter;            /* cap on CG iterations per level (per inner solve) */
   double inner_tol;        /* MIXED: inner float32 CG stops at ||r|| <= inner_tol ||r0|| */
   int max_refine;          /* MIXED: cap on refinement steps per level */
@@ -102,7 +103,16 @@ typedef struct {
   int profile;             /* nonzero: time every kernel launch of excmg_solve / excmg_cg
                               with CUDA events on the caller's stream (stats.prof_*);
                               single-problem calls only; adds two event records per launch */
+  int dsolve;              /* excmg_dsolve: how levels 0 and 1 are solved (Algorithm 1,
+                              lines 1-2) */
 } excmg_options;
+
+/* DSOLVE of Algorithm 1 (levels 0 and 1).  DIRECT: the exact discrete solution by the
+   three-dimensional discrete sine transform, which diagonalises the 19-point operator on
+   the box (grids whose interior fits one block's shared memory, about 13,000 unknowns;
+   larger coarse grids fall back to CG); stats.iters = 0 for these levels and relres the
+   residual of the direct solution.  CG: CG from zero to eps_coarse. */
+typedef enum { EXCMG_DSOLVE_DIRECT = 0, EXCMG_DSOLVE_CG = 1 } excmg_dsolve;
 
 /* Per-solve statistics, valid when the call returns. */
 typedef struct {

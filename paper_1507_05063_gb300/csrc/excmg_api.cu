@@ -122,6 +122,7 @@ bool options_ok(const excmg_options* o) {
     return false;
   if (o->fixed_iters && o->precision != EXCMG_FP64) return false;
   if (o->tile_z < 0 || o->tile_z > 256 || o->chunk < 0 || o->mixed_min_nodes < 0) return false;
+  if (o->dsolve != EXCMG_DSOLVE_DIRECT && o->dsolve != EXCMG_DSOLVE_CG) return false;
   return true;
 }
 
@@ -151,8 +152,8 @@ ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_
   const long long nf = lv.back().nodes();
   // float64 CG vectors: every level (FP64), or the levels MIXED solves in float64
   long long n64 = 0;
-  for (const Level& l : lv)
-    if (!mixed || need_fp64_vectors || l.nodes() < minn) n64 = std::max(n64, l.nodes());
+  for (size_t k = 0; k < lv.size(); ++k)  // (levels 0 and 1: DSOLVE works in float64)
+    if (!mixed || need_fp64_vectors || lv[k].nodes() < minn || k < 2) n64 = std::max(n64, lv[k].nodes());
   if (n64 > 0) {
     L.r = off;
     off = align_up(off + sizeof(double) * n64);
@@ -541,8 +542,9 @@ excmg_status solve_items(const Ctx& c, std::vector<Item>& items, const excmg_opt
   std::vector<Item> small, large;
   std::vector<int> where;
   for (auto& it : items) {
-    where.push_back(it.nodes < minn ? 0 : 1);
-    (it.nodes < minn ? small : large).push_back(it);
+    const bool fp64 = it.nodes < minn || it.d64.direct;  // DSOLVE levels stay float64
+    where.push_back(fp64 ? 0 : 1);
+    (fp64 ? small : large).push_back(it);
   }
   Ctx cs = c;
   cs.defer = false;  // MIXED calls read their states per level
@@ -606,7 +608,25 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     CK(c.timed(EXCMG_K_RESIDUAL, nodes_sum, [&] {
       return launch_residual(false, n, c.resd(), tiles, grid, c.st(), c.partials(), c.counters(), c.s);
     }));
-    excmg_status e = cg_loop<double>(c, n, c.cgd(), tiles, grid, slots, nslots, o->chunk, hs, nodes_sum, hd);
+    // DSOLVE levels: one direct solve each (their states are done with 0 steps, so the
+    // CG engines skip them)
+    int ndirect = 0;
+    size_t dsm = 0;
+    double dnodes = 0.0;
+    for (auto& it : items)
+      if (it.d64.direct) {
+        ++ndirect;
+        dsm = std::max(dsm, dsolve_smem(it.d64.g));
+        dnodes += (double)it.nodes;
+      }
+    if (ndirect > 0)
+      CK(c.timed(EXCMG_K_DSOLVE, dnodes, [&] { return launch_dsolve(n, c.cgd(), dsm, c.st(), c.s); }));
+    excmg_status e = EXCMG_OK;
+    if (ndirect < n) {
+      e = cg_loop<double>(c, n, c.cgd(), tiles, grid, slots, nslots, o->chunk, hs, nodes_sum, hd);
+    } else if (!c.defer) {
+      e = read_states(c, nslots, hs);
+    }
     if (e != EXCMG_OK) return e;
     if (c.defer) return EXCMG_OK;  // the caller reads every state at the end
     for (auto& it : items) {
@@ -714,6 +734,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   d.pa = reinterpret_cast<double*>(p.base + p.L.pa);
   d.pb = reinterpret_cast<double*>(p.base + p.L.pb);
   d.q = reinterpret_cast<double*>(p.base + p.L.q);
+  d.direct = 0;  // set by the cascade for its DSOLVE levels
   const bool res = p.L.s1 > 0 && g.nodes() <= kResidentMaxNodes;
   d.s0 = res ? reinterpret_cast<double*>(p.base + p.L.s0) : nullptr;
   d.s1 = res ? reinterpret_cast<double*>(p.base + p.L.s1) : nullptr;
@@ -729,6 +750,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   f.pb = reinterpret_cast<float*>(p.base + p.L.pb32);
   f.q = reinterpret_cast<float*>(p.base + p.L.q32);
   f.s0 = f.s1 = nullptr;
+  f.direct = 0;
   f.aux = p.level_u(l);
   f.scale = 1.0;
   it.rhs_cache = p.L.rhs64 ? reinterpret_cast<double*>(p.base + p.L.rhs64) : nullptr;
@@ -820,6 +842,9 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
     std::vector<int> fixed;
     for (int a = 0; a < na; ++a) {
       items.push_back(make_item(P[act[a]], lev[a], slot_of(act[a], lev[a]), o));
+      // DSOLVE (levels 0 and 1 of the cascade): the direct solve when the grid fits
+      CGDesc<double>& d = items.back().d64;
+      d.direct = (lev[a] < 2 && o->dsolve == EXCMG_DSOLVE_DIRECT && dsolve_fits(d.g)) ? 1 : 0;
       if (o->fixed_iters) fixed.push_back(o->fixed_iters[lev[a]]);
     }
     excmg_status e = solve_items(c, items, o, state_slots(np), o->fixed_iters ? fixed.data() : nullptr);
@@ -886,6 +911,7 @@ void excmg_default_options(excmg_options* o) {
   o->chunk = 0;
   o->mixed_min_nodes = 0;
   o->profile = 0;
+  o->dsolve = EXCMG_DSOLVE_DIRECT;
 }
 
 const char* excmg_status_string(excmg_status s) {

@@ -98,6 +98,7 @@ struct CGDesc {
                           // so float32 products neither underflow nor overflow)
   int blk_begin;          // persistent CG: this problem's blocks are [blk_begin,
   int blk_count;          //   blk_begin + blk_count) of the cooperative grid
+  int direct;             // 1: the level is solved by DSOLVE (k_dsolve), not by CG
 };
 
 // One problem of a residual phase: r = LHS(u) - RHS(f) (= b - A u_I) in float64,
@@ -190,6 +191,15 @@ bool resident_box(const Grid3& g, ResidentDesc& D, size_t& smem);
 // pairs: 2 G double2 (G = nbx nby nbz); counter, err: zeroed.
 cudaError_t launch_cg_resident(const ResidentDesc& D, size_t smem, CGState* st, double2* pairs,
                                unsigned* counter, int* err, cudaStream_t s);
+
+// DSOLVE by the discrete sine transform (dsolve_kernels.cu): one block per descriptor
+// with `direct` set (others return at once); x's interior = A^{-1} r, r = the residual
+// of the result, the CG state done with 0 steps.  dsolve_fits: the grid's interior fits
+// one block's shared memory; dsolve_smem: the bytes it needs.
+bool dsolve_fits(const Grid3& g);
+size_t dsolve_smem(const Grid3& g);
+cudaError_t launch_dsolve(int nprob, const CGDesc<double>* descs, size_t smem, CGState* st,
+                          cudaStream_t s);
 
 // Transfer kernels (transfer_kernels.cu).
 struct ProlongDesc {

@@ -27,7 +27,7 @@ MAX_LEVELS = 24
 FP64, MIXED = 0, 1
 KERNEL_NAMES = ["spmv_f64", "update_f64", "spmv_f32", "update_f32", "residual", "exp_finite",
                 "init", "correct", "exp_true", "cg_f64", "cg_f32", "cg_cluster_f64", "cg_cluster_f32",
-                "cg_resident_f64"]
+                "cg_resident_f64", "dsolve"]
 KERNEL_KINDS = len(KERNEL_NAMES)
 STATUS = {0: "EXCMG_OK", 1: "EXCMG_ERR_INVALID_ARG", 2: "EXCMG_ERR_NOT_CONVERGED",
           3: "EXCMG_ERR_CUDA", 4: "EXCMG_ERR_NONFINITE", 5: "EXCMG_ERR_TIMEOUT",
@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("fixed_iters", ctypes.POINTER(ctypes.c_int)), ("tile_z", ctypes.c_int),
                 ("chunk", ctypes.c_int), ("mixed_min_nodes", ctypes.c_longlong),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("dsolve", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -130,9 +130,12 @@ def make_grid(L, N, N0=(2, 2, 2)):
                 int(N0[0]), int(N0[1]), int(N0[2]))
 
 
+DSOLVE = {"direct": 0, "cg": 1}
+
+
 def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
                  inner_tol=1e-4, max_refine=50, fixed_iters=None, tile_z=0, chunk=0, profile=0,
-                 mixed_min_nodes=0):
+                 mixed_min_nodes=0, dsolve="direct"):
     o = Options()
     excmg_default_options(ctypes.byref(o))
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else int(precision)
@@ -145,6 +148,7 @@ def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
     o.chunk = int(chunk)
     o.profile = int(profile)
     o.mixed_min_nodes = int(mixed_min_nodes)
+    o.dsolve = DSOLVE[dsolve] if isinstance(dsolve, str) else int(dsolve)
     keep = None
     if fixed_iters is not None:
         keep = (ctypes.c_int * len(fixed_iters))(*[int(v) for v in fixed_iters])

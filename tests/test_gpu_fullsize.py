@@ -34,7 +34,7 @@ def test_512x256x128_fp64_full_cascade(X):
     res = X.solve(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), L, N0, eps=1e-9,
                   eps_coarse=1e-12, want_utilde=True)
     iters = res["stats"]["iters"]
-    ref = O.excmg(f, g, L, N, N0, eps=1e-9, eps_coarse=1e-12, fixed_iters=iters)
+    ref = O.excmg(f, g, L, N, N0, eps=1e-9, dsolve="dense", fixed_iters=iters)
     ug = res["u"].cpu().numpy()
     uo = ref["u"][-1]
     assert np.max(np.abs(ug - uo)) <= 1e-10 * np.max(np.abs(uo))

@@ -100,7 +100,7 @@ def test_batched_replays_oracle(X):
     batch = [X.BatchedProblem(L, N, N0, dev(f), dev(g)) for L, N, N0, f, g, _ in probs]
     res = X.solve_batched(batch, eps=1e-10)
     for (L, N, N0, f, g, _), ub, st in zip(probs, res["u"], res["stats"]):
-        ref = O.excmg(f, g, L, N, N0, eps=0.0, fixed_iters=st["iters"])
+        ref = O.excmg(f, g, L, N, N0, eps=0.0, dsolve="dense", fixed_iters=st["iters"])
         uo = ref["u"][-1]
         assert np.max(np.abs(host(ub) - uo)) <= 1e-10 * np.max(np.abs(uo))
 

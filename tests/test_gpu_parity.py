@@ -141,11 +141,11 @@ def test_excmg_replayed_iterations(X, name, N, N0, eps, epsc):
     f, g, u = P.make_inputs(P.PROBLEMS[name], N)
     res = X.solve(dev(f), dev(g), L, N0, eps=eps, eps_coarse=epsc, want_utilde=True)
     iters = res["stats"]["iters"]
-    ref = O.excmg(f, g, L, N, N0, eps=eps, eps_coarse=epsc, fixed_iters=iters)
+    ref = O.excmg(f, g, L, N, N0, eps=eps, dsolve="dense", fixed_iters=iters)
     assert rel_linf(host(res["u"]), ref["u"][-1]) <= TOL_SOLVE
     assert rel_linf(host(res["ut"]), ref["ut"][-1]) <= TOL_SOLVE
     # the oracle run at the tolerance takes (nearly) the same counts
-    free = O.excmg(f, g, L, N, N0, eps=eps, eps_coarse=epsc)
+    free = O.excmg(f, g, L, N, N0, eps=eps, dsolve="dense")
     assert all(abs(a - b) <= 2 for a, b in zip(iters, free["iters"])), (iters, free["iters"])
     # discretisation errors agree to 3 significant digits
     e_gpu = np.max(np.abs(host(res["u"]) - u))
@@ -154,14 +154,55 @@ def test_excmg_replayed_iterations(X, name, N, N0, eps, epsc):
 
 
 def test_excmg_oracle_fixed_counts_both_sides(X):
-    """Both sides run the same prescribed iteration counts (FP64 fixed mode)."""
+    """Both sides run the same prescribed iteration counts (FP64 fixed mode), DSOLVE as
+    CG with counts, and DSOLVE as the direct solve (the counts of levels 0-1 unused)."""
     N, N0, L = (32, 16, 16), (8, 4, 4), (1.0, 1.0, 1.0)
     f, g, _ = P.make_inputs(P.PROBLEMS["ex3"], N)
     counts = [12, 9, 6]
-    res = X.solve(dev(f), dev(g), L, N0, fixed_iters=counts)
+    res = X.solve(dev(f), dev(g), L, N0, fixed_iters=counts, dsolve="cg")
     assert res["stats"]["iters"] == counts
     ref = O.excmg(f, g, L, N, N0, eps=0.0, fixed_iters=counts)
     assert rel_linf(host(res["u"]), ref["u"][-1]) <= TOL_SOLVE
+    res = X.solve(dev(f), dev(g), L, N0, fixed_iters=counts)
+    assert res["stats"]["iters"] == [0, 0, 6]
+    ref = O.excmg(f, g, L, N, N0, eps=0.0, dsolve="dense", fixed_iters=counts)
+    assert rel_linf(host(res["u"]), ref["u"][-1]) <= TOL_SOLVE
+
+
+@pytest.mark.parametrize("N0,L", [((8, 4, 2), (1.0, 1.0, 1.0)),
+                                  ((6, 10, 4), (1.2, 0.5, 2.0)),
+                                  ((8, 6, 10), (1.0, 0.7, 1.3))])
+def test_dsolve_direct_matches_dense_cholesky(X, N0, L):
+    """DSOLVE (levels 0 and 1) by the sine transform equals the oracle's dense Cholesky
+    solve: no CG steps there, residual at rounding level, and the 3-level cascade
+    matches the oracle run with dense DSOLVE and the GPU's level-2 step count."""
+    N = tuple(4 * n for n in N0)
+    f, g, _ = P.make_inputs(P.PROBLEMS["ex3"], N, L)
+    res = X.solve(dev(f), dev(g), L, N0, eps=1e-10)
+    st = res["stats"]
+    assert st["levels"] == 3 and st["iters"][:2] == [0, 0]
+    assert max(st["relres"][:2]) <= 1e-13
+    ref = O.excmg(f, g, L, N, N0, eps=1e-10, dsolve="dense", fixed_iters=st["iters"])
+    assert rel_linf(host(res["u"]), ref["u"][-1]) <= TOL_SOLVE
+    # the CG variant of DSOLVE reaches the same answer to its tolerances
+    rcg = X.solve(dev(f), dev(g), L, N0, eps=1e-10, dsolve="cg", eps_coarse=1e-13)
+    assert min(rcg["stats"]["iters"][:2]) > 0
+    assert rel_linf(host(rcg["u"]), ref["u"][-1]) <= 1e-8
+
+
+def test_dsolve_large_coarse_grid_falls_back_to_cg(X):
+    """A coarse grid whose interior does not fit one block's shared memory (31^3
+    unknowns on level 1) is solved by CG to eps_coarse instead."""
+    N0, L = (16, 16, 16), (1.0, 1.0, 1.0)
+    N = (64, 64, 64)
+    f, g, _ = P.make_inputs(P.PROBLEMS["ex3"], N)
+    res = X.solve(dev(f), dev(g), L, N0, eps=1e-10, eps_coarse=1e-12)
+    st = res["stats"]
+    assert st["iters"][0] == 0 and st["iters"][1] > 0  # 15^3 direct, 31^3 by CG
+    assert st["relres"][1] <= 1e-12 and st["relres"][2] <= 1e-10
+    ref = O.excmg(f, g, L, N, N0, eps=1e-10, dsolve="dense", fixed_iters=st["iters"])
+    # level 1 differs from the oracle's exact level 1 by the CG tolerance only
+    assert rel_linf(host(res["u"]), ref["u"][-1]) <= 1e-8
 
 
 def test_excmg_table_errors(X):

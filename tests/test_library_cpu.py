@@ -72,3 +72,13 @@ def test_small_workspace_rejected(X):
     # misaligned workspace
     assert X.excmg_solve(ctypes.byref(g), a, b, ctypes.byref(o), ctypes.c_void_p(3 << 20), None,
                          ctypes.c_void_p((4 << 20) + 8), 1 << 34, None, None) == 6
+
+
+def test_bench_tables_cover_every_kernel_kind():
+    """bench.py reports every kernel kind the library profiles (bytes, FP64 operations,
+    symbol and source file per kind)."""
+    import bench
+    from paper_1507_05063_gb300 import excmg
+    for k in excmg.KERNEL_NAMES:
+        assert k in bench.ALGO and k in bench.KERNEL_SYMBOL and k in bench.KERNEL_SOURCE, k
+        assert os.path.exists(os.path.join(ROOT, "paper_1507_05063_gb300", "csrc", bench.KERNEL_SOURCE[k]))
