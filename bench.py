@@ -316,6 +316,7 @@ def main():
              (slice(None), slice(0, 1), slice(None)), (slice(None), slice(-1, None), slice(None)),
              (slice(None), slice(None), slice(0, 1)), (slice(None), slice(None), slice(-1, None))]
     g_faces = [torch.from_numpy(np.ascontiguousarray(g[sl])).pin_memory() for sl in faces]
+    g_stage = [torch.empty(gf.shape, dtype=torch.float64, device=device) for gf in g_faces]
     u_pin = torch.empty(f.shape, dtype=torch.float64).pin_memory()
     fd2, gd2, ud2 = torch.empty_like(fd), torch.empty_like(gd), torch.empty_like(fd)
     barrier()
@@ -325,8 +326,9 @@ def main():
     e2.record(stream)
     for _ in range(args.steps):
         fd2.copy_(f_pin, non_blocking=True)
-        for sl, gf in zip(faces, g_faces):
-            gd2[sl].copy_(gf, non_blocking=True)
+        for sl, gf, gs in zip(faces, g_faces, g_stage):
+            gs.copy_(gf, non_blocking=True)   # contiguous host -> device copy of one face
+            gd2[sl] = gs                       # then a strided device-side copy
         X.solve(fd2, gd2, L, N0, ws=ws, out=ud2, **opts)
         u_pin.copy_(ud2, non_blocking=True)
     e3.record(stream)

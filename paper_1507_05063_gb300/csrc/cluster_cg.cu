@@ -21,7 +21,7 @@
 //     previous r, w, s read through distributed shared memory (DSMEM), with the same
 //     fused operations as the owner, so it is bit-identical and no barrier is needed
 //     between the update and the stencil;
-//   * the reduction: warp sums, CTA sum in warp 0, the CTA's partials stored into slots
+//   * the reduction: values parked in shared memory, CTA sums in warp 0, stored into slots
 //     of every CTA of the cluster (DSMEM), a cluster barrier, then every CTA adds the C
 //     slots in the same order -- all CTAs hold bit-identical alpha, beta and stop
 //     decisions, so they take the same number of barriers.
@@ -83,28 +83,26 @@ __device__ __forceinline__ double xor_sum(double v, int from) {
 // Sums of (a, b) over every thread of the cluster, returned in every lane of warp 0
 // (bit-identical in every CTA); other warps get 0.  Contains one cluster barrier.
 template <int NW>
-__device__ double2 cluster_sum2(double a, double b, double* s_warp, double* slots,
+__device__ double2 cluster_sum2(double a, double b, double* s_park, double* slots,
                                 unsigned me, int csize) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  a = xor_sum(a, 16);
-  b = xor_sum(b, 16);
-  if (lane == 0) {
-    s_warp[warp] = a;
-    s_warp[NW + warp] = b;
-  }
+  // the CTA's sums: values parked in shared memory, added by warp 0 (NW per lane, then a
+  // butterfly) -- few float64 warp instructions, which share the narrow FP64 pipe
+  s_park[threadIdx.x] = a;
+  s_park[32 * NW + threadIdx.x] = b;
   __syncthreads();
   if (warp == 0) {
-    double ta = lane < NW ? s_warp[lane] : 0.0;
-    double tb = lane < NW ? s_warp[NW + lane] : 0.0;
-    if (NW > 1) {
-      ta = xor_sum(ta, NW / 2);  // lanes 0..NW-1 hold the CTA sums
-      tb = xor_sum(tb, NW / 2);
+    double ta = 0.0, tb = 0.0;
+#pragma unroll
+    for (int u = 0; u < NW; ++u) {
+      ta += s_park[lane + 32 * u];
+      tb += s_park[32 * NW + lane + 32 * u];
     }
-    // every lane takes lane 0's sums: lane c stores into CTA c, and the cluster may have
-    // more CTAs than this CTA has warps (a CTA given a wrong partial would take other
-    // decisions than its peers)
-    ta = __shfl_sync(0xffffffffu, ta, 0);
-    tb = __shfl_sync(0xffffffffu, tb, 0);
+    // a full butterfly: every lane holds the CTA's sums (lane c stores into CTA c, and
+    // the cluster may have more CTAs than this CTA has warps -- a CTA given a wrong
+    // partial would take other decisions than its peers)
+    ta = xor_sum(ta, 16);
+    tb = xor_sum(tb, 16);
     if (lane < csize) {
       st_cl(slots + me, (unsigned)lane, ta);
       st_cl(slots + kClMax + me, (unsigned)lane, tb);
@@ -143,7 +141,7 @@ __global__ void __launch_bounds__(NT)
     k_cg_cluster(const CGDesc<T>* __restrict__ descs, CGState* st, int csize) {
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char s_raw[];
-  __shared__ double s_warp[2 * NW];
+  __shared__ double s_park[2 * NT];
   // two slot sets, alternating per reduction: a peer's stores for the next reduction can
   // only start after the barrier that follows this CTA's reads of the current one
   __shared__ double s_slots[2][2 * kClMax];
@@ -210,7 +208,7 @@ __global__ void __launch_bounds__(NT)
   const int max_iter = S->max_iter, fixed = S->fixed;
   int status = EXCMG_OK;
   {
-    const double2 red = cluster_sum2<NW>(0.0, acc_d, s_warp, s_slots[0], me, csize);
+    const double2 red = cluster_sum2<NW>(0.0, acc_d, s_park, s_slots[0], me, csize);
     if (warp == 0) {
       delta = red.y;
       int stop = 0;
@@ -296,7 +294,7 @@ __global__ void __launch_bounds__(NT)
       acc_g = fma((double)rv, (double)rv, acc_g);
       acc_d = fma((double)wv, (double)rv, acc_d);
     }
-    const double2 red = cluster_sum2<NW>(acc_g, acc_d, s_warp, s_slots[par ^ 1], me, csize);
+    const double2 red = cluster_sum2<NW>(acc_g, acc_d, s_park, s_slots[par ^ 1], me, csize);
     if (warp == 0) {
       const double gn = red.x, dn = red.y;
       iter += 1;
@@ -354,7 +352,7 @@ __global__ void __launch_bounds__(NT)
   cl_sync();  // no CTA leaves while a peer could still address its shared memory
 }
 
-constexpr size_t kClStaticSmem = 1024;  // static shared memory of k_cg_cluster, rounded up
+constexpr size_t kClStaticSmem = 10 * 1024;  // static shared memory of k_cg_cluster (<= 512 threads), rounded up
 
 int g_cl_max_smem = 0;           // largest dynamic shared memory per CTA (opt-in)
 int g_cl_ok[2][5] = {};          // [T][log2 C]: 0 unknown, 1 launchable, -1 not

@@ -31,9 +31,9 @@ namespace excmg {
 namespace {
 
 constexpr int kRsThreads = 256;
-constexpr int kRsWarps = kRsThreads / 32;
 constexpr unsigned long long kRsSpinLimit = 1ull << 25;
 constexpr int kRsHB = 6;  // halo nodes per thread whose loads are issued ahead
+constexpr int kRsPB = 8;  // block partials per lane in flight
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -46,61 +46,79 @@ __device__ __forceinline__ double rs_xor_sum(double v, int from) {
   return v;
 }
 
-// Grid-wide sums of (a, b) over every thread of every block, in *s_out of every block
-// (bit-identical).  Reduction number `seq` (1, 2, ...): block b stores its partials into
-// pair b of the set seq & 1 (two sets: a block can be one reduction ahead of another's
-// reads, never two), arrives on the counter with release semantics and waits (bounded)
-// until all G blocks have arrived; then warp 0 adds the G pairs in index order.
-// Returns false if the wait ran out or another block reported a time-out.
-__device__ bool rs_grid_sum2(double a, double b, double2* pairs, unsigned* counter, int G,
-                             unsigned seq, int* err, double* s_warp, double2* s_out, int* s_ok) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  a = rs_xor_sum(a, 16);
-  b = rs_xor_sum(b, 16);
-  if (lane == 0) {
-    s_warp[warp] = a;
-    s_warp[kRsWarps + warp] = b;
-  }
+// Block sums of (a, b): every thread parks its values in shared memory and warp 0 adds
+// them (kRsThreads / 32 per lane, then a butterfly) -- a handful of float64 warp
+// instructions instead of a butterfly in every warp.  Sums valid in warp 0.
+__device__ double2 rs_block_sum2(double a, double b, double* s_park) {
+  s_park[threadIdx.x] = a;
+  s_park[kRsThreads + threadIdx.x] = b;
   __syncthreads();
-  double2* set = pairs + (size_t)(seq & 1) * G;
-  if (warp == 0) {
-    double ta = lane < kRsWarps ? s_warp[lane] : 0.0;
-    double tb = lane < kRsWarps ? s_warp[kRsWarps + lane] : 0.0;
-    ta = rs_xor_sum(ta, kRsWarps / 2);
-    tb = rs_xor_sum(tb, kRsWarps / 2);
-    if (lane == 0) {
-      __stcg(&set[blockIdx.x], make_double2(ta, tb));
-      // release: this block's partials and (through the block barrier above) every
-      // store of its threads become visible before the arrival
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
-      const unsigned target = seq * (unsigned)G;
-      int ok = 1;
-      unsigned long long spins = 0;
-      while (ld_acquire_u32(counter) < target) {
-        if (++spins > kRsSpinLimit || *(volatile int*)err) {
-          ok = 0;
-          break;
-        }
-        if (spins > 4096) __nanosleep(64);
-      }
-      if (!ok) atomicExch(err, 1);
-      *s_ok = ok;
+  double2 t = make_double2(0.0, 0.0);
+  if (threadIdx.x < 32) {
+    double ta = 0.0, tb = 0.0;
+#pragma unroll
+    for (int u = 0; u < kRsThreads / 32; ++u) {
+      ta += s_park[threadIdx.x + 32 * u];
+      tb += s_park[kRsThreads + threadIdx.x + 32 * u];
     }
-    __syncwarp();
-    double sa = 0.0, sb = 0.0;
-    if (*(volatile int*)s_ok) {
-      for (int i = lane; i < G; i += 32) {
-        const double2 v = __ldcg(&set[i]);
-        sa += v.x;
-        sb += v.y;
+    t = make_double2(rs_xor_sum(ta, 16), rs_xor_sum(tb, 16));
+  }
+  return t;
+}
+
+// Reduction number `seq` (1, 2, ...): thread 0 stores this block's partials as pair b of
+// the set seq & 1 (two sets: a block can be one reduction ahead of another's reads, never
+// two), arrives on the counter with release semantics -- which also publishes every
+// global store the block's threads made before the block barrier that precedes this
+// call -- and waits (bounded) until all G blocks have arrived.  Returns, in every
+// thread, false if the wait ran out or another block reported a time-out.
+__device__ bool rs_arrive_wait(double2 part, double2* pairs, unsigned* counter, int G, unsigned seq,
+                               int* err, int* s_ok) {
+  if (threadIdx.x == 0) {
+    __stcg(&pairs[(size_t)(seq & 1) * G + blockIdx.x], part);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
+    const unsigned target = seq * (unsigned)G;
+    int ok = 1;
+    unsigned long long spins = 0;
+    while (ld_acquire_u32(counter) < target) {
+      if (++spins > kRsSpinLimit || *(volatile int*)err) {
+        ok = 0;
+        break;
       }
+      if (spins > 4096) __nanosleep(64);
     }
-    sa = rs_xor_sum(sa, 16);
-    sb = rs_xor_sum(sb, 16);
-    if (lane == 0) *s_out = make_double2(sa, sb);
+    if (!ok) atomicExch(err, 1);
+    *s_ok = ok;
   }
   __syncthreads();
   return *s_ok != 0;
+}
+
+// Warp 0, after the wait: the sums of the G pairs of set seq & 1, in a fixed order (lane
+// l takes pairs l, l + 32, ...: kRsPB loads in flight, a tree within the lane, then a
+// butterfly), identical in every lane and every block.
+__device__ double2 rs_read_pairs(const double2* pairs, int G, unsigned seq) {
+  const double2* set = pairs + (size_t)(seq & 1) * G;
+  const int lane = threadIdx.x & 31;
+  double sa = 0.0, sb = 0.0;
+  for (int i0 = 0; i0 < G; i0 += 32 * kRsPB) {
+    double2 v[kRsPB];
+#pragma unroll
+    for (int u = 0; u < kRsPB; ++u) {
+      const int i = i0 + lane + 32 * u;
+      v[u] = i < G ? __ldcg(&set[i]) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int w = 1; w < kRsPB; w *= 2)
+#pragma unroll
+      for (int u = 0; u + w < kRsPB; u += 2 * w) {
+        v[u].x += v[u + w].x;
+        v[u].y += v[u + w].y;
+      }
+    sa += v[0].x;
+    sb += v[0].y;
+  }
+  return make_double2(rs_xor_sum(sa, 16), rs_xor_sum(sb, 16));
 }
 
 // 19-point A-stencil at offset 0 of P with strides (1, ey, ez).
@@ -115,8 +133,7 @@ __device__ __forceinline__ double rs_stencil(const double* P, int ey, int ez, co
 __global__ void __launch_bounds__(kRsThreads)
     k_cg_resident(const ResidentDesc D, CGState* st, double2* pairs, unsigned* counter, int* err) {
   extern __shared__ __align__(16) double s_vec[];
-  __shared__ double s_warp[2 * kRsWarps];
-  __shared__ double2 s_red;
+  __shared__ double s_park[2 * kRsThreads];
   __shared__ int s_ok;
   __shared__ double s_alpha, s_beta;
   __shared__ int s_stop;
@@ -213,44 +230,22 @@ __global__ void __launch_bounds__(kRsThreads)
     }
     W[q] = w;
   }
+  // CG scalars: warp 0 keeps identical copies in all its lanes (and in every block)
   double gam = S->rr, alpha = 0.0, beta = 0.0, delta = 0.0;
   const double tol2 = S->tol2;
   int iter = S->iter;
   const int max_iter = S->max_iter, fixed = S->fixed;
   int status = EXCMG_OK;
-  unsigned seq = 1;
-  if (!rs_grid_sum2(0.0, acc_d, pairs, counter, G, seq++, err, s_warp, &s_red, &s_ok)) {
-    status = EXCMG_ERR_TIMEOUT;
-    s_stop = 1;
-  } else if (threadIdx.x == 0) {
-    delta = s_red.y;
-    int stop = 0;
-    if (delta == 0.0 && gam == 0.0) {
-      stop = 1;  // exact solution (fixed-count mode)
-    } else if (!(delta > 0.0) || !isfinite(delta)) {
-      status = EXCMG_ERR_NONFINITE;
-      stop = 1;
-    } else {
-      alpha = gam / delta;
-    }
-    s_stop = stop;
-    s_alpha = alpha;
-    s_beta = 0.0;
-  }
-  __syncthreads();
-  int par = 0;  // step i reads the published r_i, w_i, s_{i-1} of parity par
-  while (!s_stop) {
-    const double a = s_alpha, bt = s_beta;
+  const int lane = threadIdx.x & 31;
+  // the published r, w, s of up to kRsHB halo nodes per thread, loaded right after each
+  // reduction's wait, so that the load latency overlaps the reading of the partials and
+  // the scalar arithmetic (zero on the boundary)
+  double hr[kRsHB], hw[kRsHB], hs[kRsHB];
+  int he[kRsHB];
+  auto load_halo = [&](int par) {
     const double* Rg = par ? D.r1 : D.r;
     const double* Wg = par ? D.w1 : D.w0;
     const double* Sg = par ? D.s1 : D.s0;
-    double* Rn = par ? D.r : D.r1;
-    double* Wn = par ? D.w0 : D.w1;
-    double* Sn = par ? D.s0 : D.s1;
-    // 1. the halo's published r, w, s: the loads of up to kRsHB shell nodes per thread
-    // are issued first, so that their latency overlaps the own-node update
-    double hr[kRsHB], hw[kRsHB], hs[kRsHB];
-    int he[kRsHB];
 #pragma unroll
     for (int u = 0; u < kRsHB; ++u) {
       const int h = threadIdx.x + u * kRsThreads;
@@ -267,7 +262,47 @@ __global__ void __launch_bounds__(kRsThreads)
         }
       }
     }
-    // 2. own nodes: p, s, x, r; publish r and s
+  };
+  unsigned seq = 1;
+  {
+    const double2 part = rs_block_sum2(0.0, acc_d, s_park);
+    const bool ok = rs_arrive_wait(part, pairs, counter, G, seq, err, &s_ok);
+    if (ok) load_halo(0);
+    if (threadIdx.x < 32) {
+      int stop = 0;
+      if (!ok) {
+        status = EXCMG_ERR_TIMEOUT;
+        stop = 1;
+      } else {
+        delta = rs_read_pairs(pairs, G, seq).y;
+        if (delta == 0.0 && gam == 0.0) {
+          stop = 1;  // exact solution (fixed-count mode)
+        } else if (!(delta > 0.0) || !isfinite(delta)) {
+          status = EXCMG_ERR_NONFINITE;
+          stop = 1;
+        } else {
+          alpha = gam / delta;
+        }
+      }
+      if (lane == 0) {
+        s_stop = stop;
+        s_alpha = alpha;
+        s_beta = 0.0;
+      }
+    }
+    ++seq;
+    __syncthreads();
+  }
+  int par = 0;  // step i reads the published r_i, w_i, s_{i-1} of parity par
+  while (!s_stop) {
+    const double a = s_alpha, bt = s_beta;
+    const double* Rg = par ? D.r1 : D.r;
+    const double* Wg = par ? D.w1 : D.w0;
+    const double* Sg = par ? D.s1 : D.s0;
+    double* Rn = par ? D.r : D.r1;
+    double* Wn = par ? D.w0 : D.w1;
+    double* Sn = par ? D.s0 : D.s1;
+    // 1. own nodes: p, s, x, r; publish r and s
     for (int q = threadIdx.x; q < B; q += kRsThreads) {
       const Own n = own_node(q);
       if (!n.valid) continue;
@@ -284,9 +319,8 @@ __global__ void __launch_bounds__(kRsThreads)
       __stcg(Rn + o, rn);
       __stcg(Sn + o, sv);
     }
-    // 3. the halo's new r, with the owner's fused operations (zero on the boundary: the
-    // loads above left r = w = s = 0 there); shells larger than kRsHB per thread finish
-    // with plain loads
+    // 2. the halo's new r, with the owner's fused operations; shells larger than kRsHB
+    // per thread finish with plain loads
 #pragma unroll
     for (int u = 0; u < kRsHB; ++u)
       if (he[u] >= 0) R[he[u]] = fma(-a, fma(bt, hs[u], hw[u]), hr[u]);
@@ -301,7 +335,7 @@ __global__ void __launch_bounds__(kRsThreads)
       R[e] = rn;
     }
     __syncthreads();
-    // 4. w = A r, gamma, delta; publish w
+    // 3. w = A r, gamma, delta; publish w
     double acc_g = 0.0;
     acc_d = 0.0;
     for (int q = threadIdx.x; q < B; q += kRsThreads) {
@@ -316,16 +350,20 @@ __global__ void __launch_bounds__(kRsThreads)
       }
       W[q] = w;
     }
-    // 5. the grid reduction (it also orders every block's publications before the next
-    // step's halo loads), scalars
-    const bool ok = rs_grid_sum2(acc_g, acc_d, pairs, counter, G, seq++, err, s_warp, &s_red, &s_ok);
-    if (threadIdx.x == 0) {
+    // 4. the grid reduction (it also orders every block's publications before the next
+    // step's halo loads); the next halo's loads; scalars
+    const double2 part = rs_block_sum2(acc_g, acc_d, s_park);
+    const bool ok = rs_arrive_wait(part, pairs, counter, G, seq, err, &s_ok);
+    par ^= 1;
+    if (ok) load_halo(par);
+    if (threadIdx.x < 32) {
       int stop = 0;
       if (!ok) {
         status = EXCMG_ERR_TIMEOUT;
         stop = 1;
       } else {
-        const double gn = s_red.x, dn = s_red.y;
+        const double2 red = rs_read_pairs(pairs, G, seq);
+        const double gn = red.x, dn = red.y;
         iter += 1;
         if (!isfinite(gn) || !isfinite(dn)) {
           status = EXCMG_ERR_NONFINITE;
@@ -336,26 +374,30 @@ __global__ void __launch_bounds__(kRsThreads)
           if (!fixed) status = EXCMG_ERR_NOT_CONVERGED;
           stop = 1;
         } else {
-          // alpha' = gn / (dn - beta' gn / alpha) = gn k / (dn k - gn^2), k = gam alpha
+          // alpha' = gn / (dn - beta' gn / alpha) = gn k / (dn k - gn^2), k = gam alpha;
+          // beta' = gn / gam: both divides in one instruction (lanes 0 and 1)
           const double k = gam * alpha;
           const double den = fma(dn, k, -gn * gn);
           if (!(den > 0.0)) {
             status = EXCMG_ERR_NONFINITE;
             stop = 1;
           } else {
-            alpha = gn * k / den;
-            beta = gn / gam;
+            const double q = (lane == 0 ? gn * k : gn) / (lane == 0 ? den : gam);
+            alpha = __shfl_sync(0xffffffffu, q, 0);
+            beta = __shfl_sync(0xffffffffu, q, 1);
           }
         }
         gam = gn;
         delta = dn;
       }
-      s_stop = stop;
-      s_alpha = alpha;
-      s_beta = beta;
+      if (lane == 0) {
+        s_stop = stop;
+        s_alpha = alpha;
+        s_beta = beta;
+      }
     }
+    ++seq;
     __syncthreads();
-    par ^= 1;
   }
   // x and the last r of the box
   for (int q = threadIdx.x; q < B; q += kRsThreads) {
