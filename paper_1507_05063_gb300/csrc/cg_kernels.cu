@@ -719,6 +719,29 @@ __global__ void __launch_bounds__(kThreads)
     // boundary part: b = LHS(boundary part of u) - RHS(f)
     double Cm1 = 0, Tm1 = 0, Tm2 = 0, LCm1 = 0, LTm1 = 0, LTm2 = 0;
     const bool use_f = d.src == nullptr;
+#ifdef EXCMG_RESIDUAL_L1
+    // the 3x3 neighbourhood of column (i, j) in plane kk, read through the read-only
+    // cache (neighbouring threads share the lines): no staging and no block barrier
+    auto load_n = [&](int kk, double* v) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) v[q] = 0.0;
+      if (kk < 0 || kk > g.nz) return;
+      const double* pl = u + (long long)kk * g.sz;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const int gi = i + (q % 3) - 1, gj = j + (q / 3) - 1;
+        if (gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny) v[q] = __ldg(pl + gi + gj * g.sy);
+      }
+    };
+    // (no software prefetch: without block barriers the warps march independently and
+    // hide each other's load latency)
+    for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
+      const bool plane_bnd = (kk == 0) || (kk == g.nz);
+      double nb[9];
+      load_n(kk, nb);
+      const double SW = nb[0], S = nb[1], SE = nb[2], W = nb[3], P = nb[4], E = nb[5];
+      const double NW = nb[6], N = nb[7], NE = nb[8];
+#else
     // the (kTX+2) x (kTY+2) plane of u, at most two elements per thread; the loads of
     // plane kk+1 are issued before the barrier and arithmetic of plane kk
     auto load_u = [&](int kk, double& a0, double& a1) {
@@ -752,6 +775,7 @@ __global__ void __launch_bounds__(kThreads)
       const double S = su[buf][ty][tx + 1], N = su[buf][ty + 2][tx + 1];
       const double SW = su[buf][ty][tx], SE = su[buf][ty][tx + 2];
       const double NW = su[buf][ty + 2][tx], NE = su[buf][ty + 2][tx + 2];
+#endif
       const double SX = W + E, SY = S + N, EXY = (SW + SE) + (NW + NE);
       const double Ck = fma(A.c0, P, fma(A.fx, SX, fma(A.fy, SY, A.exy * EXY)));
       const double Tk = fma(A.fz, P, fma(A.exz, SX, A.eyz * SY));

@@ -349,10 +349,10 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
   // launch where problem p gets a team of blocks and iterates on its own.
   const int coop = persistent_cg_blocks<T>();
   // a single float64 grid that fits the resident CG (vectors in shared memory)
-  // (grids small enough for one cluster stay on the cluster kernel below: its exchange
-  // through distributed shared memory beats the global round trips of the resident one)
+  // (the smallest grids stay on the cluster kernel below: its exchange through
+  // distributed shared memory beats the global round trips of the resident one there)
   if (n == 1 && sizeof(T) == 8 && c.persistent_ok && hd[0].s0 && hd[0].s1 &&
-      hd[0].g.nodes() > kClusterMaxNodes && hd[0].g.nodes() <= kResidentMaxNodes) {
+      hd[0].g.nodes() > kResidentMinNodes && hd[0].g.nodes() <= kResidentMaxNodes) {
     ResidentDesc D;
     memset(&D, 0, sizeof(D));
     size_t smem = 0;

@@ -1,8 +1,9 @@
 """The three CG engines, each on grid sizes that select it, against the oracle.
 
 excmg_cg (and every level of excmg_solve) runs a float64 grid's CG steps on one of:
-  * k_cg_cluster   -- up to 20,000 nodes, one thread-block cluster of 1-16 CTAs;
-  * k_cg_resident  -- up to 2^19 nodes, a cooperative grid with the vectors in shared
+  * k_cg_cluster   -- up to 2,000 nodes (and the small grids of batched solves, up to
+                      20,000), one thread-block cluster of 1-16 CTAs;
+  * k_cg_resident  -- 2,000 to 2^19 nodes, a cooperative grid with the vectors in shared
                       memory (3D boxes, partial boxes at the far faces);
   * k_cg_persistent -- larger grids, streaming from HBM.
 The first two use the single-reduction recurrence (same iterates as the oracle's standard
@@ -51,8 +52,8 @@ ENGINE_CASES = [
     ((8, 4, 2), (1.0, 1.0, 1.0), "cg_cluster_f64", 10),       # 135: one CTA
     ((16, 8, 4), (1.0, 0.5, 0.25), "cg_cluster_f64", 15),     # 765: 8 CTAs of 4 warps
     ((24, 10, 6), (1.0, 0.7, 0.3), "cg_cluster_f64", 15),     # 1,925: last CTA partial
-    ((32, 16, 8), (1.0, 1.0, 1.0), "cg_cluster_f64", 20),     # 5,049: 16 CTAs
-    ((40, 24, 12), (1.0, 0.8, 0.4), "cg_cluster_f64", 20),    # 13,325: 16 CTAs of 16 warps
+    ((32, 16, 8), (1.0, 1.0, 1.0), "cg_resident_f64", 20),    # 5,049
+    ((40, 24, 12), (1.0, 0.8, 0.4), "cg_resident_f64", 20),   # 13,325
     ((64, 32, 16), (1.0, 1.0, 1.0), "cg_resident_f64", 20),   # 36,465
     ((50, 36, 22), (1.0, 0.9, 0.6), "cg_resident_f64", 20),   # 43,401: partial boxes
     ((128, 64, 32), (1.0, 1.0, 1.0), "cg_resident_f64", 12),  # 276,705
@@ -72,7 +73,7 @@ def test_engine_fixed_steps(X, N, L, engine, k):
 
 
 @pytest.mark.parametrize("N,L,engine", [((16, 8, 4), (1.0, 1.0, 1.0), "cg_cluster_f64"),
-                                        ((40, 24, 12), (1.0, 0.8, 0.4), "cg_cluster_f64"),
+                                        ((40, 24, 12), (1.0, 0.8, 0.4), "cg_resident_f64"),
                                         ((64, 32, 16), (1.0, 1.0, 1.0), "cg_resident_f64"),
                                         ((50, 36, 22), (1.0, 0.9, 0.6), "cg_resident_f64")])
 def test_engine_tolerance_stop(X, N, L, engine):
