@@ -669,11 +669,13 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
 // ---------------------------------------------------------------------------------
 // K3: r = LHS(u) - RHS(f) = b - A u_I (float64), sums r.r and b.b, CG state init
 // ---------------------------------------------------------------------------------
+#ifndef EXCMG_RES_MINB
+#define EXCMG_RES_MINB 3  // 24 warps per SM (80 registers, a few spills): measured faster
+#endif
 template <typename TR>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
     k_residual(int nprob, const ResDesc* __restrict__ descs, long long total_tiles,
                CGState* st, double* partials, unsigned* counters) {
-  __shared__ double su[2][kTY + 2][kTX + 2];
   __shared__ int s_active[kMaxProb];
   __shared__ double s_part[2 * kMaxProb];
   for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
@@ -683,7 +685,7 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncthreads();
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-  int buf = 0, cur = -1, p = 0;
+  int cur = -1, p = 0;
   // acc_b4 sums (2 b)^2 over nodes whose stencil misses the boundary (there b = -RHS)
   double acc_r = 0.0, acc_b = 0.0, acc_b4 = 0.0;
   for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -719,7 +721,6 @@ __global__ void __launch_bounds__(kThreads)
     // boundary part: b = LHS(boundary part of u) - RHS(f)
     double Cm1 = 0, Tm1 = 0, Tm2 = 0, LCm1 = 0, LTm1 = 0, LTm2 = 0;
     const bool use_f = d.src == nullptr;
-#ifdef EXCMG_RESIDUAL_L1
     // the 3x3 neighbourhood of column (i, j) in plane kk, read through the read-only
     // cache (neighbouring threads share the lines): no staging and no block barrier
     auto load_n = [&](int kk, double* v) {
@@ -741,41 +742,6 @@ __global__ void __launch_bounds__(kThreads)
       load_n(kk, nb);
       const double SW = nb[0], S = nb[1], SE = nb[2], W = nb[3], P = nb[4], E = nb[5];
       const double NW = nb[6], N = nb[7], NE = nb[8];
-#else
-    // the (kTX+2) x (kTY+2) plane of u, at most two elements per thread; the loads of
-    // plane kk+1 are issued before the barrier and arithmetic of plane kk
-    auto load_u = [&](int kk, double& a0, double& a1) {
-      a0 = a1 = 0.0;
-      if (kk < 0 || kk > g.nz) return;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int idx = threadIdx.x + h * kThreads;
-        if (idx >= kStage) break;
-        const int ly = idx / (kTX + 2), lx = idx - ly * (kTX + 2);
-        const int gi = c.x0 - 1 + lx, gj = c.y0 - 1 + ly;
-        if (gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny) {
-          const double v = u[gi + gj * g.sy + (long long)kk * g.sz];
-          if (h == 0) a0 = v; else a1 = v;
-        }
-      }
-    };
-    double n0, n1;
-    load_u(c.z0 - 1, n0, n1);
-    for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
-      const bool plane_bnd = (kk == 0) || (kk == g.nz);
-      {
-        double* flat = &su[buf][0][0];
-        flat[threadIdx.x] = n0;
-        if (threadIdx.x + kThreads < kStage) flat[threadIdx.x + kThreads] = n1;
-      }
-      if (kk < c.z1) load_u(kk + 1, n0, n1);
-      __syncthreads();
-      const double P = su[buf][ty + 1][tx + 1];
-      const double W = su[buf][ty + 1][tx], E = su[buf][ty + 1][tx + 2];
-      const double S = su[buf][ty][tx + 1], N = su[buf][ty + 2][tx + 1];
-      const double SW = su[buf][ty][tx], SE = su[buf][ty][tx + 2];
-      const double NW = su[buf][ty + 2][tx], NE = su[buf][ty + 2][tx + 2];
-#endif
       const double SX = W + E, SY = S + N, EXY = (SW + SE) + (NW + NE);
       const double Ck = fma(A.c0, P, fma(A.fx, SX, fma(A.fy, SY, A.exy * EXY)));
       const double Tk = fma(A.fz, P, fma(A.exz, SX, A.eyz * SY));
@@ -828,7 +794,6 @@ __global__ void __launch_bounds__(kThreads)
       LTm2 = LTm1;
       LTm1 = LTk;
       LCm1 = LCk;
-      buf ^= 1;
     }
   }
   if (cur >= 0) {

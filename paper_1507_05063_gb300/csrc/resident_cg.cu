@@ -456,7 +456,8 @@ bool resident_box(const Grid3& g, ResidentDesc& D, size_t& smem) {
   if (ni < 1 || nj < 1 || nk < 1) return false;
   const long long max_blocks = std::min<long long>((long long)g_rs_sms * g_rs_blocks_per_sm, kMaxGrid);
   // per-step model in SM clocks: the busiest SM's float64 work (~12.5 clocks per node,
-  // 2 DFMA per clock) plus the halo loads of a box (3 per shell node)
+  // 2 DFMA per clock, plus ~400 per block for its reduction), the halo loads of a box
+  // (3 per shell node), and the grid reduction's share per block (arrival, partials)
   double best = 1e300;
   bool found = false;
   const int bxs[] = {32, 16, 8};
@@ -472,7 +473,7 @@ bool resident_box(const Grid3& g, ResidentDesc& D, size_t& smem) {
         const double B = (double)bx * by * bz;
         const double shell = (double)(bx + 2) * (by + 2) * (bz + 2) - B;
         const double per_sm = (double)((nb + g_rs_sms - 1) / g_rs_sms);
-        const double cost = per_sm * B * 12.5 + shell * 6.0;
+        const double cost = per_sm * (B * 12.5 + 400.0) + shell * 6.0 + (double)nb * 12.0;
         if (cost < best) {
           best = cost;
           found = true;
