@@ -105,6 +105,11 @@ typedef struct {
                               single-problem calls only; adds two event records per launch */
   int dsolve;              /* excmg_dsolve: how levels 0 and 1 are solved (Algorithm 1,
                               lines 1-2) */
+  double eps_ratio;        /* per-level tolerance: level l >= 2 of L levels stops at
+                              eps * eps_ratio^(L-1-l), so the finest level uses eps and each
+                              coarser one eps_ratio times more (64 = 2^6 follows the
+                              sixth-order error of u~ from level to level); 1 (the default)
+                              or 0: the uniform eps of Algorithm 1 */
 } excmg_options;
 
 /* DSOLVE of Algorithm 1 (levels 0 and 1).  DIRECT: the exact discrete solution by the

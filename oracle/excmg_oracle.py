@@ -447,7 +447,7 @@ def level_sizes(N, N0):
 
 
 def excmg(f, g, L, N, N0, eps, eps_coarse=1e-12, max_iter=100000, dsolve="cg",
-          fixed_iters=None, want_utilde=True):
+          fixed_iters=None, want_utilde=True, eps_ratio=1.0):
     """EXCMG(A_h, f_h, L, eps) of Algorithm 1.
 
     ``f``, ``g``: finest-grid node arrays (g read on boundary nodes only).  ``L``: box
@@ -455,6 +455,9 @@ def excmg(f, g, L, N, N0, eps, eps_coarse=1e-12, max_iter=100000, dsolve="cg",
     (CG to ``eps_coarse`` or dense Cholesky); every finer level starts CG from
     w_h = EXP_finite(u_2h, u_4h) and stops at ||r|| <= eps ||b||; ũ_h =
     EXP_true(u_h, u_2h).  ``fixed_iters`` (one count per level) replaces both tests.
+    ``eps_ratio`` r: level l >= 2 of the nl levels stops at eps * r**(nl-1-l) (the
+    uniform eps of Algorithm 1 when r = 1; r = 2**6 follows the sixth-order error of
+    the extrapolated solution from level to level, Section 5's remark on uniform eps).
     Returns a dict of per-level lists: 'u', 'w', 'ut', 'iters', 'relres', 'h', 'N'.
     """
     sizes = level_sizes(N, N0)
@@ -476,7 +479,8 @@ def excmg(f, g, L, N, N0, eps, eps_coarse=1e-12, max_iter=100000, dsolve="cg",
             w = None
         else:
             w = exp_finite(out["u"][l - 1], out["u"][l - 2])
-            ul, it, rel = cg(with_boundary(w, gl), fl, hl, eps, max_iter, fixed)
+            eps_l = eps * eps_ratio ** (len(sizes) - 1 - l)
+            ul, it, rel = cg(with_boundary(w, gl), fl, hl, eps_l, max_iter, fixed)
         out["u"].append(ul)
         out["w"].append(w)
         out["iters"].append(it)

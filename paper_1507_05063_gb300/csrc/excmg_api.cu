@@ -123,6 +123,7 @@ bool options_ok(const excmg_options* o) {
   if (o->fixed_iters && o->precision != EXCMG_FP64) return false;
   if (o->tile_z < 0 || o->tile_z > 256 || o->chunk < 0 || o->mixed_min_nodes < 0) return false;
   if (o->dsolve != EXCMG_DSOLVE_DIRECT && o->dsolve != EXCMG_DSOLVE_CG) return false;
+  if (!(o->eps_ratio >= 0) || !std::isfinite(o->eps_ratio)) return false;
   return true;
 }
 
@@ -721,7 +722,8 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   const Tiling t = make_tiling(g, tz);
   Item it;
   memset(&it, 0, sizeof(it));
-  it.eps = (l < 2) ? o->eps_coarse : o->eps;
+  const double ratio = o->eps_ratio > 0 ? o->eps_ratio : 1.0;
+  it.eps = (l < 2) ? o->eps_coarse : o->eps * std::pow(ratio, (double)((int)p.lv.size() - 1 - l));
   it.nodes = g.nodes();
   it.res = make_res(g, t, slot, p.level_u(l), p.fview(l), nullptr);
   CGDesc<double>& d = it.d64;
@@ -912,6 +914,7 @@ void excmg_default_options(excmg_options* o) {
   o->mixed_min_nodes = 0;
   o->profile = 0;
   o->dsolve = EXCMG_DSOLVE_DIRECT;
+  o->eps_ratio = 1.0;
 }
 
 const char* excmg_status_string(excmg_status s) {

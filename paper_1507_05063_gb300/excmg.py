@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("fixed_iters", ctypes.POINTER(ctypes.c_int)), ("tile_z", ctypes.c_int),
                 ("chunk", ctypes.c_int), ("mixed_min_nodes", ctypes.c_longlong),
-                ("profile", ctypes.c_int), ("dsolve", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("dsolve", ctypes.c_int), ("eps_ratio", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -135,7 +135,7 @@ DSOLVE = {"direct": 0, "cg": 1}
 
 def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
                  inner_tol=1e-4, max_refine=50, fixed_iters=None, tile_z=0, chunk=0, profile=0,
-                 mixed_min_nodes=0, dsolve="direct"):
+                 mixed_min_nodes=0, dsolve="direct", eps_ratio=1.0):
     o = Options()
     excmg_default_options(ctypes.byref(o))
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else int(precision)
@@ -149,6 +149,7 @@ def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
     o.profile = int(profile)
     o.mixed_min_nodes = int(mixed_min_nodes)
     o.dsolve = DSOLVE[dsolve] if isinstance(dsolve, str) else int(dsolve)
+    o.eps_ratio = float(eps_ratio)
     keep = None
     if fixed_iters is not None:
         keep = (ctypes.c_int * len(fixed_iters))(*[int(v) for v in fixed_iters])

@@ -190,6 +190,21 @@ def test_dsolve_direct_matches_dense_cholesky(X, N0, L):
     assert rel_linf(host(rcg["u"]), ref["u"][-1]) <= 1e-8
 
 
+def test_per_level_tolerance_replays_oracle(X):
+    """eps_ratio: each level l >= 2 meets eps * r^(L-1-l) in the GPU's float64 residual,
+    and the oracle run with the same per-level tolerances and step counts agrees."""
+    N, N0, L = (64, 32, 16), (8, 4, 2), (1.0, 1.0, 1.0)
+    f, g, _ = P.make_inputs(P.PROBLEMS["ex4"], N)
+    eps, r = 1e-12, 64.0
+    res = X.solve(dev(f), dev(g), L, N0, eps=eps, eps_ratio=r)
+    st = res["stats"]
+    nl = st["levels"]
+    for l in range(2, nl):
+        assert st["relres"][l] <= eps * r ** (nl - 1 - l) * 1.0000001
+    ref = O.excmg(f, g, L, N, N0, eps=eps, dsolve="dense", eps_ratio=r, fixed_iters=st["iters"])
+    assert rel_linf(host(res["u"]), ref["u"][-1]) <= TOL_SOLVE
+
+
 def test_dsolve_large_coarse_grid_falls_back_to_cg(X):
     """A coarse grid whose interior does not fit one block's shared memory (31^3
     unknowns on level 1) is solved by CG to eps_coarse instead."""

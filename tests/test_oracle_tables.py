@@ -77,3 +77,21 @@ def test_dense_dsolve_agrees_with_cg_dsolve():
     b = O.excmg(f, g, (1, 1, 1), N, (4, 4, 4), eps=1e-13, dsolve="dense")
     assert np.max(np.abs(a["u"][1] - b["u"][1])) < 1e-12
     assert np.max(np.abs(a["u"][-1] - b["u"][-1])) < 1e-11
+
+
+def test_per_level_tolerance():
+    """eps_ratio r: level l >= 2 of nl levels stops at eps * r**(nl-1-l); r = 1 is the
+    uniform tolerance of Algorithm 1 (identical run)."""
+    N, N0, eps = (32, 32, 32), (4, 4, 4), 1e-12
+    f, g, _ = P.make_inputs(P.PROBLEMS["ex1"], N)
+    base = O.excmg(f, g, (1, 1, 1), N, N0, eps=eps, dsolve="dense")
+    same = O.excmg(f, g, (1, 1, 1), N, N0, eps=eps, dsolve="dense", eps_ratio=1.0)
+    assert base["iters"] == same["iters"]
+    assert np.array_equal(base["u"][-1], same["u"][-1])
+    r = 64.0
+    res = O.excmg(f, g, (1, 1, 1), N, N0, eps=eps, dsolve="dense", eps_ratio=r)
+    nl = len(res["N"])
+    for l in range(2, nl):
+        assert res["relres"][l] <= eps * r ** (nl - 1 - l)
+    # looser coarse levels never take more steps than the uniform run there
+    assert all(a <= b for a, b in zip(res["iters"][2:-1], base["iters"][2:-1]))
