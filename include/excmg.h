@@ -73,7 +73,9 @@ typedef enum {
   EXCMG_K_CG_RESIDENT_F64 = 13, /* all CG steps of a mid-size grid, vectors resident in the
                                    blocks' shared memory (float64) */
   EXCMG_K_DSOLVE = 14,    /* direct solve of a coarse level (discrete sine transform) */
-  EXCMG_KERNEL_KINDS = 15
+  EXCMG_K_PROLONG_CMP = 15, /* w_h by a comparison prolongation (options.prolong QUADRATIC
+                               or LINEAR) in place of EXP_finite */
+  EXCMG_KERNEL_KINDS = 16
 } excmg_kernel_kind;
 
 /* Box and grids (Section 2: hx = Lx/Nx ...; Algorithm 1: coarsest grid H, L levels). */
@@ -110,6 +112,8 @@ typedef struct {
                               coarser one eps_ratio times more (64 = 2^6 follows the
                               sixth-order error of u~ from level to level); 1 (the default)
                               or 0: the uniform eps of Algorithm 1 */
+  int prolong;             /* excmg_prolong: how the initial guess w_h of levels >= 2 is
+                              formed (Algorithm 1, line 6); default QUARTIC */
 } excmg_options;
 
 /* DSOLVE of Algorithm 1 (levels 0 and 1).  DIRECT: the exact discrete solution by the
@@ -118,6 +122,18 @@ typedef struct {
    larger coarse grids fall back to CG); stats.iters = 0 for these levels and relres the
    residual of the direct solution.  CG: CG from zero to eps_coarse. */
 typedef enum { EXCMG_DSOLVE_DIRECT = 0, EXCMG_DSOLVE_CG = 1 } excmg_dsolve;
+
+/* Initial guess of levels >= 2 (Algorithm 1, line 6).  QUARTIC: EXP_finite(u_2h, u_4h) --
+   extrapolation to the grid-2h nodes (eqs. jiedian, zhongdian), then tri-quartic
+   interpolation over cells of 2x2x2 grid-4h elements (eq. inter); the method of the paper.
+   The other two exist to measure what EXP_finite saves: QUADRATIC keeps the extrapolation
+   and interpolates tri-quadratically over cells of 2x2x2 grid-2h elements (the
+   interpolation of the earlier EXCMG for linear finite elements, which the first remark of
+   Section 3.3 finds too inaccurate for the fourth-order scheme); LINEAR is the cascadic
+   multigrid prolongation of Section 3: trilinear interpolation of u_2h alone, no
+   extrapolation.  All three write the Dirichlet data on the boundary. */
+typedef enum { EXCMG_PROLONG_QUARTIC = 0, EXCMG_PROLONG_QUADRATIC = 1,
+               EXCMG_PROLONG_LINEAR = 2 } excmg_prolong;
 
 /* Per-solve statistics, valid when the call returns. */
 typedef struct {
@@ -162,8 +178,15 @@ size_t excmg_workspace_size(const excmg_grid* grid, const excmg_options* opt);
  *                  nodes).
  *   g        [in]  finest-grid node array; only boundary entries are read (Dirichlet
  *                  data).
- *   u        [out] finest-grid node array: the FD solution u_h, boundary = g.
- *   u_tilde  [out] NULL, or a finest-grid node array receiving EXP_true(u_h, u_2h).
+ *                  f and g may be device memory, or page-locked host memory mapped into
+ *                  the device's address space (cudaHostAlloc, or cudaHostRegister with
+ *                  cudaHostRegisterMapped; the same address on host and device): the
+ *                  kernels then read them over the host link while they compute, with
+ *                  no separate copy.  Any other pointer returns EXCMG_ERR_INVALID_ARG.
+ *   u        [out] finest-grid node array in device memory: the FD solution u_h,
+ *                  boundary = g.
+ *   u_tilde  [out] NULL, or a finest-grid node array in device memory receiving
+ *                  EXP_true(u_h, u_2h).
  *   ws, ws_bytes   workspace of at least excmg_workspace_size(grid, opt) bytes.
  *   stats    [out] NULL or host struct.
  * Returns EXCMG_ERR_NOT_CONVERGED if any level hit max_iter (u then holds the last

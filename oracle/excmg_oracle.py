@@ -43,7 +43,8 @@ __all__ = [
     "lagrange_basis", "triquartic_cell_matrix", "extrapolate_fd", "exp_finite", "with_boundary",
     "extrapolate_true", "gradient", "excmg", "level_sizes", "l2_norm", "linf_norm",
     "grad_l2_norm", "grad_linf_norm", "adjoint", "rhs_transpose", "lift_transpose",
-    "meshsizes", "observed_order",
+    "meshsizes", "observed_order", "lagrange_cell_matrix", "prolong_quadratic",
+    "prolong_linear", "prolong",
 ]
 
 
@@ -370,6 +371,81 @@ def exp_finite(u2h, u4h):
     return fine
 
 
+# Comparison prolongations (the library's ``prolong`` option): what EXP_finite is measured
+# against.  Section 3.3's first remark: the tri-quadratic interpolation of the earlier
+# EXCMG (linear finite elements) is too inaccurate for the fourth-order scheme; Section 3:
+# cascadic multigrid prolongs by linear interpolation alone.
+
+def lagrange_cell_matrix(P):
+    """Tensor-product Lagrange interpolation with P nodes per direction on one cell.
+
+    The cell has P known nodes per direction at natural coordinates 0, 1, ..., P-1 and
+    the fine nodes at the half steps 0, 1/2, ..., P-1.  Returns (M, fine_idx) like
+    ``triquartic_cell_matrix``: one row per fine node that is not a known node, one
+    column per known node (index (k*P + j)*P + i), entries l_i(xi) l_j(eta) l_k(zeta)
+    with the P-point basis of ``lagrange_basis``.
+    """
+    nodes = tuple(range(P))
+    nf = 2 * P - 1
+    rows, fine_idx = [], []
+    for c in range(nf):
+        for b in range(nf):
+            for a in range(nf):
+                if a % 2 == 0 and b % 2 == 0 and c % 2 == 0:
+                    continue
+                row = np.empty(P ** 3)
+                for k in range(P):
+                    for j in range(P):
+                        for i in range(P):
+                            row[(k * P + j) * P + i] = (lagrange_basis(i, a / 2.0, nodes)
+                                                        * lagrange_basis(j, b / 2.0, nodes)
+                                                        * lagrange_basis(k, c / 2.0, nodes))
+                rows.append(row)
+                fine_idx.append((c, b, a))
+    return np.array(rows), fine_idx
+
+
+def _interpolate_cells(W, P):
+    """Fine grid (half the spacing of W's grid) from the values W at its even nodes, by
+    ``lagrange_cell_matrix(P)`` on every cell of (P-1)^3 elements of W's grid."""
+    C = P - 1
+    nz2, ny2, nx2 = W.shape
+    assert (nz2 - 1) % C == 0 and (ny2 - 1) % C == 0 and (nx2 - 1) % C == 0, \
+        "the grid must hold whole interpolation cells"
+    ncz, ncy, ncx = (nz2 - 1) // C, (ny2 - 1) // C, (nx2 - 1) // C
+    M, fine_idx = lagrange_cell_matrix(P)
+    fine = np.empty((2 * nz2 - 1, 2 * ny2 - 1, 2 * nx2 - 1))
+    fine[0::2, 0::2, 0::2] = W
+    windows = np.lib.stride_tricks.sliding_window_view(W, (P, P, P))[::C, ::C, ::C]
+    vals = windows.reshape(ncz * ncy * ncx, P ** 3) @ M.T
+    vals = vals.reshape(ncz, ncy, ncx, len(fine_idx))
+    for col, (c, b, a) in enumerate(fine_idx):
+        fine[c:c + 2 * C * ncz:2 * C, b:b + 2 * C * ncy:2 * C, a:a + 2 * C * ncx:2 * C] = vals[..., col]
+    return fine
+
+
+def prolong_quadratic(u2h, u4h):
+    """The extrapolation of EXP_finite (``extrapolate_fd``) at the nodes of grid 2h, then
+    tri-quadratic interpolation on every cell of 2x2x2 elements of grid 2h."""
+    return _interpolate_cells(extrapolate_fd(u2h, u4h), 3)
+
+
+def prolong_linear(u2h):
+    """Cascadic multigrid: trilinear interpolation of u_2h alone (no extrapolation)."""
+    return _interpolate_cells(np.asarray(u2h, dtype=np.float64), 2)
+
+
+def prolong(kind, u2h, u4h):
+    """w_h of Algorithm 1, line 6, by the named prolongation ('quartic' = EXP_finite)."""
+    if kind == "quartic":
+        return exp_finite(u2h, u4h)
+    if kind == "quadratic":
+        return prolong_quadratic(u2h, u4h)
+    if kind == "linear":
+        return prolong_linear(u2h)
+    raise ValueError(kind)
+
+
 def with_boundary(w, g):
     """Copy of w whose boundary nodes hold the Dirichlet data g (Section 2)."""
     out = np.array(g, dtype=np.float64, copy=True)
@@ -447,7 +523,7 @@ def level_sizes(N, N0):
 
 
 def excmg(f, g, L, N, N0, eps, eps_coarse=1e-12, max_iter=100000, dsolve="cg",
-          fixed_iters=None, want_utilde=True, eps_ratio=1.0):
+          fixed_iters=None, want_utilde=True, eps_ratio=1.0, prolong_kind="quartic"):
     """EXCMG(A_h, f_h, L, eps) of Algorithm 1.
 
     ``f``, ``g``: finest-grid node arrays (g read on boundary nodes only).  ``L``: box
@@ -458,6 +534,8 @@ def excmg(f, g, L, N, N0, eps, eps_coarse=1e-12, max_iter=100000, dsolve="cg",
     ``eps_ratio`` r: level l >= 2 of the nl levels stops at eps * r**(nl-1-l) (the
     uniform eps of Algorithm 1 when r = 1; r = 2**6 follows the sixth-order error of
     the extrapolated solution from level to level, Section 5's remark on uniform eps).
+    ``prolong_kind``: 'quartic' (EXP_finite, the method), or the comparison
+    prolongations 'quadratic' / 'linear' (``prolong``).
     Returns a dict of per-level lists: 'u', 'w', 'ut', 'iters', 'relres', 'h', 'N'.
     """
     sizes = level_sizes(N, N0)
@@ -478,7 +556,7 @@ def excmg(f, g, L, N, N0, eps, eps_coarse=1e-12, max_iter=100000, dsolve="cg",
                 ul, it, rel = cg(start, fl, hl, eps_coarse, max_iter, fixed)
             w = None
         else:
-            w = exp_finite(out["u"][l - 1], out["u"][l - 2])
+            w = prolong(prolong_kind, out["u"][l - 1], out["u"][l - 2])
             eps_l = eps * eps_ratio ** (len(sizes) - 1 - l)
             ul, it, rel = cg(with_boundary(w, gl), fl, hl, eps_l, max_iter, fixed)
         out["u"].append(ul)

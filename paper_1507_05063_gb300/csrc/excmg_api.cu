@@ -124,6 +124,9 @@ bool options_ok(const excmg_options* o) {
   if (o->tile_z < 0 || o->tile_z > 256 || o->chunk < 0 || o->mixed_min_nodes < 0) return false;
   if (o->dsolve != EXCMG_DSOLVE_DIRECT && o->dsolve != EXCMG_DSOLVE_CG) return false;
   if (!(o->eps_ratio >= 0) || !std::isfinite(o->eps_ratio)) return false;
+  if (o->prolong != EXCMG_PROLONG_QUARTIC && o->prolong != EXCMG_PROLONG_QUADRATIC &&
+      o->prolong != EXCMG_PROLONG_LINEAR)
+    return false;
   return true;
 }
 
@@ -837,7 +840,13 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
     }
     if (npro > 0) {
       CK(cudaMemcpyAsync(c.prold(), hp.data(), sizeof(ProlongDesc) * npro, cudaMemcpyHostToDevice, c.s));
-      CK(c.timed(EXCMG_K_EXP_FINITE, pnodes, [&] { return launch_exp_finite(npro, c.prold(), pblocks, c.s); }));
+      if (o->prolong == EXCMG_PROLONG_QUARTIC) {
+        CK(c.timed(EXCMG_K_EXP_FINITE, pnodes, [&] { return launch_exp_finite(npro, c.prold(), pblocks, c.s); }));
+      } else {
+        const int points = o->prolong == EXCMG_PROLONG_QUADRATIC ? 3 : 2;
+        CK(c.timed(EXCMG_K_PROLONG_CMP, pnodes,
+                   [&] { return launch_prolong_cmp(points, npro, c.prold(), pblocks, c.s); }));
+      }
     }
     // 2. CG (FP64) or refinement (MIXED) on every active problem's level
     std::vector<Item> items;
@@ -895,6 +904,27 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// Memory the current device's kernels may read: device or managed memory, or
+// page-locked host memory mapped at the same address (read over the host link).
+bool device_readable(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
+bool device_memory(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" {
@@ -915,6 +945,7 @@ void excmg_default_options(excmg_options* o) {
   o->profile = 0;
   o->dsolve = EXCMG_DSOLVE_DIRECT;
   o->eps_ratio = 1.0;
+  o->prolong = EXCMG_PROLONG_QUARTIC;
 }
 
 const char* excmg_status_string(excmg_status s) {
@@ -966,6 +997,10 @@ excmg_status excmg_solve(const excmg_grid* grid, const double* f, const double* 
       if (opt->fixed_iters[l] < 0) return EXCMG_ERR_INVALID_ARG;
   const size_t need = excmg_workspace_size(grid, opt);
   if (!ws || ws_bytes < need || !aligned(ws, kAlign)) return EXCMG_ERR_WORKSPACE;
+  // where the arrays live (a driver query, after the plain argument checks)
+  if (!device_readable(f) || !device_readable(g) || !device_memory(u) ||
+      (u_tilde && !device_memory(u_tilde)))
+    return EXCMG_ERR_INVALID_ARG;
   Ctx c;
   c.ws = static_cast<char*>(ws);
   c.H = header_layout(1);

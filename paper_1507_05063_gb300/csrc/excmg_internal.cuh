@@ -220,6 +220,10 @@ struct ProlongDesc {
 cudaError_t launch_exp_finite(int nprob, const ProlongDesc* descs, long long total_blocks,
                               cudaStream_t s);
 cudaError_t launch_exp_finite_one(const ProlongDesc& desc, cudaStream_t s);
+// The comparison prolongations: points = 3 (extrapolation, then tri-quadratic) or 2
+// (trilinear interpolation of u_2h); same descriptors and brick grid as EXP_finite.
+cudaError_t launch_prolong_cmp(int points, int nprob, const ProlongDesc* descs,
+                               long long total_blocks, cudaStream_t s);
 cudaError_t launch_exp_true(const Grid3& g, const double* uh, const double* u2h, double* ut,
                             cudaStream_t s);
 cudaError_t launch_boundary_init(const Grid3& g, View gb, double* u, cudaStream_t s);

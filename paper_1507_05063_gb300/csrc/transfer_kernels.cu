@@ -19,6 +19,13 @@
 // Every pass splits its outputs by parity (copies at even positions, arithmetic at odd
 // ones) so that the float64 work of a warp runs with all lanes active: on GB300 a warp
 // instruction on the narrow FP64 pipe costs the same whether 16 or 32 lanes need it.
+//
+// The same brick code, instantiated with fewer interpolation points, gives the two
+// comparison prolongations of the library's prolong option: the extrapolated grid-2h
+// values interpolated tri-quadratically over cells of 2x2x2 grid-2h elements (the
+// interpolation of the earlier EXCMG for linear elements, which the first remark of
+// Section 3.3 contrasts with the tri-quartic one), and plain trilinear interpolation of
+// u_2h with no extrapolation (the cascadic multigrid prolongation of Section 3).
 #include <math.h>
 
 #include <algorithm>
@@ -38,6 +45,11 @@ __constant__ double c_wq[4][5] = {
     {-5.0 / 128, 28.0 / 128, -70.0 / 128, 140.0 / 128, 35.0 / 128},
 };
 
+// 8 * l_m(t) of the quadratic basis on the nodes 0, 1, 2 at t = 1/2, 3/2, and the linear
+// interpolation at the midpoint of two nodes (both exact in binary floating point).
+__constant__ double c_wquad[2][3] = {{3.0 / 8, 6.0 / 8, -1.0 / 8}, {-1.0 / 8, 6.0 / 8, 3.0 / 8}};
+__constant__ double c_wlin[1][2] = {{0.5, 0.5}};
+
 constexpr int BX1 = 17, BY1 = 5, BZ1 = 5;  // grid-2h nodes of a brick
 constexpr int BX0 = 9, BY0 = 3, BZ0 = 3;   // grid-4h nodes of a brick
 constexpr int BXF = 33, BYF = 9, BZF = 9;  // fine nodes of a brick
@@ -52,8 +64,14 @@ struct BrickSmem {
   double y[BZ1][BYF][BXF];    // after the quartic pass along y
 };
 
-// One brick (local index lb) of EXP_finite for descriptor d.
+// One brick (local index lb) of the prolongation for descriptor d.  P interpolation
+// points per direction over cells of P - 1 grid-2h elements: 5 is EXP_finite (eq. inter);
+// 3 the tri-quadratic comparison; 2 the trilinear one, which also skips the
+// extrapolation (w = u_2h at the grid-2h nodes).  The brick (16 x 4 x 4 grid-2h
+// elements) holds whole cells for each P.
+template <int P>
 __device__ void exp_finite_brick(const ProlongDesc& d, long long lb, BrickSmem& S) {
+  constexpr int C = P - 1;  // grid-2h elements per cell and direction
   const Grid3 g = d.g;
   const int bx = (int)(lb % d.nbx);
   const int by = (int)((lb / d.nbx) % d.nby);
@@ -69,6 +87,13 @@ __device__ void exp_finite_brick(const ProlongDesc& d, long long lb, BrickSmem& 
   };
   __syncthreads();  // shared buffers of the previous brick are free
   // 1a. stage grid-2h values; corner sums of d along x (even columns: d, odd: d_a + d_b)
+  if (P == 2) {  // no extrapolation: w = u_2h
+    for (int idx = threadIdx.x; idx < BZ1 * BY1 * BX1; idx += kThreads) {
+      const int ix = idx % BX1, jy = (idx / BX1) % BY1, kz = idx / (BX1 * BY1);
+      const int I = 16 * bx + ix, J = 4 * by + jy, K = 4 * bz + kz;
+      S.w[kz][jy][ix] = (I <= n1x && J <= n1y && K <= n1z) ? d.u2h[I + J * s1y + K * s1z] : 0.0;
+    }
+  } else {
   for (int idx = threadIdx.x; idx < BZ1 * BY1 * BX1; idx += kThreads) {
     const int ix = idx % BX1, jy = (idx / BX1) % BY1, kz = idx / (BX1 * BY1);
     const int I = 16 * bx + ix, J = 4 * by + jy, K = 4 * bz + kz;
@@ -105,35 +130,37 @@ __device__ void exp_finite_brick(const ProlongDesc& d, long long lb, BrickSmem& 
     const double scale = 0.03125 / (double)(1 << ((ix & 1) + (jy & 1)));
     S.w[2 * k0 + 1][jy][ix] = fma(S.ty[k0][jy][ix] + S.ty[k0 + 1][jy][ix], scale, S.u1[2 * k0 + 1][jy][ix]);
   }
+  }  // P != 2
   __syncthreads();
-  // 2a. quartic along x: even fine columns are grid-2h columns
+  // 2a. interpolation along x: even fine columns are grid-2h columns
   for (int idx = threadIdx.x; idx < BZ1 * BY1 * BX1; idx += kThreads) {
     const int ix = idx % BX1, jy = (idx / BX1) % BY1, kz = idx / (BX1 * BY1);
     S.x[kz][jy][2 * ix] = S.w[kz][jy][ix];
   }
   for (int idx = threadIdx.x; idx < BZ1 * BY1 * (BX1 - 1); idx += kThreads) {
     const int I = idx % (BX1 - 1), jy = (idx / (BX1 - 1)) % BY1, kz = idx / ((BX1 - 1) * BY1);
-    const int t = I & 3, base = I - t;
+    const int t = I % C, base = I - t;
     double v = 0.0;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) v = fma(S.wq[t][m], S.w[kz][jy][base + m], v);
+    for (int m = 0; m < P; ++m) v = fma(S.wq[t][m], S.w[kz][jy][base + m], v);
     S.x[kz][jy][2 * I + 1] = v;
   }
   __syncthreads();
-  // 2b. quartic along y
+  // 2b. along y (odd fine row 2q + 1 lies in the cell starting at grid-2h row q - q % C)
   for (int idx = threadIdx.x; idx < BZ1 * BY1 * BXF; idx += kThreads) {
     const int lx = idx % BXF, jy = (idx / BXF) % BY1, kz = idx / (BXF * BY1);
     S.y[kz][2 * jy][lx] = S.x[kz][jy][lx];
   }
   for (int idx = threadIdx.x; idx < BZ1 * (BY1 - 1) * BXF; idx += kThreads) {
-    const int lx = idx % BXF, t = (idx / BXF) % (BY1 - 1), kz = idx / (BXF * (BY1 - 1));
+    const int lx = idx % BXF, q = (idx / BXF) % (BY1 - 1), kz = idx / (BXF * (BY1 - 1));
+    const int t = q % C, base = q - t;
     double v = 0.0;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) v = fma(S.wq[t][m], S.x[kz][m][lx], v);
-    S.y[kz][2 * t + 1][lx] = v;
+    for (int m = 0; m < P; ++m) v = fma(S.wq[t][m], S.x[kz][base + m][lx], v);
+    S.y[kz][2 * q + 1][lx] = v;
   }
   __syncthreads();
-  // 2c. quartic along z, boundary data, store.  Main part: the 32 x 8 x 8 nodes whose
+  // 2c. along z, boundary data, store.  Main part: the 32 x 8 x 8 nodes whose
   // brick-local coordinates are all below the brick's far faces -- one fine plane per
   // pass of the block, one row of 32 nodes per warp (uniform parity, coalesced stores).
   const bool has_g = d.gb.p != nullptr;
@@ -141,10 +168,10 @@ __device__ void exp_finite_brick(const ProlongDesc& d, long long lb, BrickSmem& 
     const bool bnd = gx == 0 || gx == g.nx || gy == 0 || gy == g.ny || gz == 0 || gz == g.nz;
     if (bnd && has_g) return d.gb.at(gx, gy, gz);
     if ((lz & 1) == 0) return S.y[lz >> 1][ly][lx];
-    const int t = (lz - 1) >> 1;
+    const int q = (lz - 1) >> 1, t = q % C, base = q - t;
     double v = 0.0;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) v = fma(S.wq[t][m], S.y[m][ly][lx], v);
+    for (int m = 0; m < P; ++m) v = fma(S.wq[t][m], S.y[base + m][ly][lx], v);
     return v;
   };
   for (int idx = threadIdx.x; idx < 32 * 8 * 8; idx += kThreads) {
@@ -167,25 +194,45 @@ __device__ void exp_finite_brick(const ProlongDesc& d, long long lb, BrickSmem& 
   }
 }
 
+// Weights of the P-point interpolation at the C = P - 1 half-integer points of a cell.
+template <int P>
 __device__ __forceinline__ void load_weights(BrickSmem& S) {
-  if (threadIdx.x < 20) S.wq[threadIdx.x / 5][threadIdx.x % 5] = c_wq[threadIdx.x / 5][threadIdx.x % 5];
+  constexpr int C = P - 1;
+  if (threadIdx.x < C * P) {
+    const int t = threadIdx.x / P, m = threadIdx.x % P;
+    S.wq[t][m] = P == 5 ? c_wq[t][m] : (P == 3 ? c_wquad[t][m] : c_wlin[t][m]);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void prolong_bricks(int nprob, const ProlongDesc* __restrict__ descs,
+                                               long long total_blocks, BrickSmem& S) {
+  load_weights<P>(S);
+  int p = 0;
+  for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) {
+    while (p + 1 < nprob && b >= descs[p + 1].block_begin) ++p;
+    exp_finite_brick<P>(descs[p], b - descs[p].block_begin, S);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads)
     k_exp_finite(int nprob, const ProlongDesc* __restrict__ descs, long long total_blocks) {
   __shared__ BrickSmem S;
-  load_weights(S);
-  int p = 0;
-  for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) {
-    while (p + 1 < nprob && b >= descs[p + 1].block_begin) ++p;
-    exp_finite_brick(descs[p], b - descs[p].block_begin, S);
-  }
+  prolong_bricks<5>(nprob, descs, total_blocks, S);
+}
+
+// The comparison prolongations (P = 3: extrapolation + tri-quadratic; P = 2: trilinear).
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+    k_prolong_cmp(int nprob, const ProlongDesc* __restrict__ descs, long long total_blocks) {
+  __shared__ BrickSmem S;
+  prolong_bricks<P>(nprob, descs, total_blocks, S);
 }
 
 __global__ void __launch_bounds__(kThreads) k_exp_finite_one(ProlongDesc d, long long total_blocks) {
   __shared__ BrickSmem S;
-  load_weights(S);
-  for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) exp_finite_brick(d, b, S);
+  load_weights<5>(S);
+  for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) exp_finite_brick<5>(d, b, S);
 }
 
 // EXP_true: u~ = u_h + (1/15) (mean of d = u_h - u_2h over the grid-2h corners of the
@@ -291,6 +338,22 @@ cudaError_t launch_exp_finite(int nprob, const ProlongDesc* descs, long long tot
   const long long wave = brick_wave((const void*)k_exp_finite, g_wave_many);
   const long long grid = std::max(1LL, std::min(total_blocks, wave));
   k_exp_finite<<<(int)grid, kThreads, 0, s>>>(nprob, descs, total_blocks);
+  return cudaGetLastError();
+}
+
+static int g_wave_quad = 0, g_wave_lin = 0;
+
+cudaError_t launch_prolong_cmp(int points, int nprob, const ProlongDesc* descs,
+                               long long total_blocks, cudaStream_t s) {
+  if (points != 3 && points != 2) return cudaErrorInvalidValue;
+  const void* k = points == 3 ? (const void*)k_prolong_cmp<3> : (const void*)k_prolong_cmp<2>;
+  const long long wave = brick_wave(k, points == 3 ? g_wave_quad : g_wave_lin);
+  const long long grid = std::max(1LL, std::min(total_blocks, wave));
+  if (points == 3) {
+    k_prolong_cmp<3><<<(int)grid, kThreads, 0, s>>>(nprob, descs, total_blocks);
+  } else {
+    k_prolong_cmp<2><<<(int)grid, kThreads, 0, s>>>(nprob, descs, total_blocks);
+  }
   return cudaGetLastError();
 }
 

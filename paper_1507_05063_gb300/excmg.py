@@ -27,7 +27,7 @@ MAX_LEVELS = 24
 FP64, MIXED = 0, 1
 KERNEL_NAMES = ["spmv_f64", "update_f64", "spmv_f32", "update_f32", "residual", "exp_finite",
                 "init", "correct", "exp_true", "cg_f64", "cg_f32", "cg_cluster_f64", "cg_cluster_f32",
-                "cg_resident_f64", "dsolve"]
+                "cg_resident_f64", "dsolve", "prolong_cmp"]
 KERNEL_KINDS = len(KERNEL_NAMES)
 STATUS = {0: "EXCMG_OK", 1: "EXCMG_ERR_INVALID_ARG", 2: "EXCMG_ERR_NOT_CONVERGED",
           3: "EXCMG_ERR_CUDA", 4: "EXCMG_ERR_NONFINITE", 5: "EXCMG_ERR_TIMEOUT",
@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("fixed_iters", ctypes.POINTER(ctypes.c_int)), ("tile_z", ctypes.c_int),
                 ("chunk", ctypes.c_int), ("mixed_min_nodes", ctypes.c_longlong),
-                ("profile", ctypes.c_int), ("dsolve", ctypes.c_int), ("eps_ratio", ctypes.c_double)]
+                ("profile", ctypes.c_int), ("dsolve", ctypes.c_int), ("eps_ratio", ctypes.c_double),
+                ("prolong", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -131,11 +132,12 @@ def make_grid(L, N, N0=(2, 2, 2)):
 
 
 DSOLVE = {"direct": 0, "cg": 1}
+PROLONG = {"quartic": 0, "quadratic": 1, "linear": 2}
 
 
 def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
                  inner_tol=1e-4, max_refine=50, fixed_iters=None, tile_z=0, chunk=0, profile=0,
-                 mixed_min_nodes=0, dsolve="direct", eps_ratio=1.0):
+                 mixed_min_nodes=0, dsolve="direct", eps_ratio=1.0, prolong="quartic"):
     o = Options()
     excmg_default_options(ctypes.byref(o))
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else int(precision)
@@ -150,6 +152,7 @@ def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
     o.mixed_min_nodes = int(mixed_min_nodes)
     o.dsolve = DSOLVE[dsolve] if isinstance(dsolve, str) else int(dsolve)
     o.eps_ratio = float(eps_ratio)
+    o.prolong = PROLONG[prolong] if isinstance(prolong, str) else int(prolong)
     keep = None
     if fixed_iters is not None:
         keep = (ctypes.c_int * len(fixed_iters))(*[int(v) for v in fixed_iters])
@@ -167,11 +170,15 @@ def _ptr(t: Optional[torch.Tensor]):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _node_array(t: torch.Tensor, N, name):
+def _node_array(t: torch.Tensor, N, name, host_ok=False):
     shape = (N[2] + 1, N[1] + 1, N[0] + 1)
     if tuple(t.shape) != shape or t.dtype != torch.float64:
         raise ValueError(f"{name}: expected float64 tensor of shape {shape}, got "
                          f"{t.dtype} {tuple(t.shape)}")
+    if host_ok and not t.is_cuda and t.is_pinned():
+        if not t.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())  # page-locked host memory, read by the kernels
     return _ptr(t)
 
 
@@ -193,19 +200,24 @@ def solve_workspace_bytes(L, N, N0, **opts) -> int:
 
 def solve(f, g, L, N0, want_utilde=False, stream=None, ws=None, out=None, allow_not_converged=False,
           **opts):
-    """Algorithm 1 on the GPU.  Returns dict(u, ut, stats, status)."""
+    """Algorithm 1 on the GPU.  Returns dict(u, ut, stats, status).
+
+    f and g may be CUDA tensors or pinned (page-locked) CPU tensors; the kernels read the
+    latter over the host link.  u, u~ and the workspace are on the GPU."""
     N = (f.shape[2] - 1, f.shape[1] - 1, f.shape[0] - 1)
     grid = make_grid(L, N, N0)
     o, _keep = make_options(**opts)
     need = excmg_workspace_size(ctypes.byref(grid), ctypes.byref(o))
     if need == 0:
         raise ExcmgError(1, "excmg_workspace_size")
+    dev = f.device if f.is_cuda else (out.device if out is not None else
+                                      torch.device("cuda", torch.cuda.current_device()))
     if ws is None or ws.numel() < need:
-        ws = workspace(need, f.device)
-    u = torch.empty_like(f) if out is None else out
-    ut = torch.empty_like(f) if want_utilde else None
+        ws = workspace(need, dev)
+    u = torch.empty(f.shape, dtype=f.dtype, device=dev) if out is None else out
+    ut = torch.empty(f.shape, dtype=f.dtype, device=dev) if want_utilde else None
     st = Stats()
-    status = excmg_solve(ctypes.byref(grid), _node_array(f, N, "f"), _node_array(g, N, "g"),
+    status = excmg_solve(ctypes.byref(grid), _node_array(f, N, "f", True), _node_array(g, N, "g", True),
                          ctypes.byref(o), _node_array(u, N, "u"), _ptr(ut), _ptr(ws),
                          ws.numel(), ctypes.byref(st), _stream(stream))
     _check(status, "excmg_solve", allow=(2,) if allow_not_converged else ())

@@ -179,3 +179,106 @@ def test_gradient_3d_exact_for_tensor_quartics():
                                rtol=1e-10, atol=1e-9)
     np.testing.assert_allclose(gz, np.broadcast_to(pv(x, cx) * pv(y, cy) * pv(z, pd(cz)), shape),
                                rtol=1e-10, atol=1e-9)
+
+
+# ---- comparison prolongations (tri-quadratic after extrapolation; trilinear) ----
+
+@pytest.mark.parametrize("P_", [2, 3])
+def test_lagrange_cell_matrix_reproduces_its_degree_only(P_):
+    """P nodes per direction reproduce every polynomial of degree < P in each variable at
+    the half steps of the cell, and not x^P."""
+    M, idx = O.lagrange_cell_matrix(P_)
+    assert M.shape == ((2 * P_ - 1) ** 3 - P_ ** 3, P_ ** 3)
+    rng = np.random.default_rng(P_)
+    c = rng.standard_normal((P_, P_, P_))
+
+    def poly(x, y, z):
+        return sum(c[p, q, r] * x ** p * y ** q * z ** r
+                   for p, q, r in itertools.product(range(P_), repeat=3))
+    rng_nodes = range(P_)
+    known = np.array([poly(i, j, k) for k in rng_nodes for j in rng_nodes for i in rng_nodes])
+    want = np.array([poly(a / 2, b / 2, cc / 2) for cc, b, a in idx])
+    np.testing.assert_allclose(M @ known, want, rtol=1e-12, atol=1e-12)
+    knownP = np.array([float(i) ** P_ for k in rng_nodes for j in rng_nodes for i in rng_nodes])
+    wantP = np.array([(a / 2) ** P_ for cc, b, a in idx])
+    assert np.max(np.abs(M @ knownP - wantP)) > 1e-2
+    # every row is a partition of unity
+    np.testing.assert_allclose(M.sum(axis=1), 1.0, rtol=0, atol=1e-14)
+
+
+def test_quadratic_weights_by_hand():
+    """1D quadratic Lagrange on nodes 0, 1, 2 at t = 1/2: (3, 6, -1)/8; at 3/2: (-1, 6, 3)/8."""
+    M, idx = O.lagrange_cell_matrix(3)
+    row = {t: r for r, t in zip(M, idx)}
+    np.testing.assert_array_equal(row[(0, 0, 1)][:3], [3 / 8, 6 / 8, -1 / 8])
+    np.testing.assert_array_equal(row[(0, 0, 3)][:3], [-1 / 8, 6 / 8, 3 / 8])
+
+
+def test_prolong_linear_is_trilinear_interpolation():
+    """CMG prolongation: exact for trilinear functions on any grid; a body centre is the
+    mean of its 8 corners."""
+    rng = np.random.default_rng(5)
+    ca = rng.standard_normal((2, 2, 2))
+    L = (1.0, 0.5, 2.0)
+
+    def A(x, y, z):
+        return sum(ca[p, q, r] * x ** p * y ** q * z ** r
+                   for p, q, r in itertools.product(range(2), repeat=3))
+    N1, N2 = (6, 4, 2), (12, 8, 4)
+    on = lambda N: np.broadcast_to(A(*P.node_coords(L, N)), (N[2] + 1, N[1] + 1, N[0] + 1))
+    np.testing.assert_allclose(O.prolong_linear(on(N1)), on(N2), rtol=1e-13, atol=1e-13)
+    u = rng.standard_normal((5, 4, 7))
+    w = O.prolong_linear(u)
+    assert w[3, 1, 5] == pytest.approx(u[1:3, 0:2, 2:4].mean(), rel=1e-14)
+    np.testing.assert_array_equal(w[::2, ::2, ::2], u)
+
+
+@pytest.mark.parametrize("N2", [(16, 8, 24), (8, 8, 8)])
+def test_prolong_quadratic_exact_under_error_expansion(N2):
+    """Extrapolation + tri-quadratic: if u^i = U + A h_i^4 with trilinear A and
+    tri-quadratic U, w^2 = u^2 everywhere; with a tri-quartic U it is not (the
+    interpolation is then the error, as the first remark of Section 3.3 says)."""
+    rng = np.random.default_rng(7)
+    L = (1.0, 1.0, 1.0)
+    ca = rng.standard_normal((2, 2, 2))
+    N1 = tuple(n // 2 for n in N2)
+    N0 = tuple(n // 4 for n in N2)
+
+    def levels(deg):
+        cu = rng.standard_normal((deg + 1,) * 3)
+
+        def fn(x, y, z, s):
+            U = sum(cu[p, q, r] * x ** p * y ** q * z ** r
+                    for p, q, r in itertools.product(range(deg + 1), repeat=3))
+            A = sum(ca[p, q, r] * x ** p * y ** q * z ** r
+                    for p, q, r in itertools.product(range(2), repeat=3))
+            return U + s * 1e-3 * A
+        on = lambda N, s: np.broadcast_to(fn(*P.node_coords(L, N), s),
+                                          (N[2] + 1, N[1] + 1, N[0] + 1)).astype(np.float64)
+        return on(N0, 256.0), on(N1, 16.0), on(N2, 1.0)
+    u0, u1, u2 = levels(2)
+    np.testing.assert_allclose(O.prolong_quadratic(u1, u0), u2, rtol=1e-12, atol=1e-11)
+    u0, u1, u2 = levels(4)
+    assert np.max(np.abs(O.prolong_quadratic(u1, u0) - u2)) > 1e-6
+
+
+def test_prolongation_orders_on_example1():
+    """||w_h - u_h||_2 on Example 1 (16^3 -> 32^3): EXP_finite is fifth order (Tables 1-2);
+    extrapolation + tri-quadratic falls to the interpolation's third order; trilinear CMG
+    to second order.  The finest-grid CG step counts follow the same ranking."""
+    prob = P.PROBLEMS["ex1"]
+    orders, iters = {}, {}
+    for kind in ("quartic", "quadratic", "linear"):
+        errs = []
+        for N in [(16, 16, 16), (32, 32, 32)]:
+            f, g, _ = P.make_inputs(prob, N)
+            res = O.excmg(f, g, (1, 1, 1), N, (4, 4, 4), eps=1e-10, dsolve="dense",
+                          want_utilde=False, prolong_kind=kind)
+            w = O.with_boundary(res["w"][-1], g)
+            errs.append(O.l2_norm(w - res["u"][-1]))
+            iters[kind] = res["iters"][-1]
+        orders[kind] = O.observed_order(errs[0], errs[1])
+    assert 4.7 < orders["quartic"] < 5.4
+    assert 2.5 < orders["quadratic"] < 3.4
+    assert 1.6 < orders["linear"] < 2.3
+    assert iters["quartic"] < iters["quadratic"] < iters["linear"]
