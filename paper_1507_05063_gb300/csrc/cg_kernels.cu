@@ -670,12 +670,68 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
 // K3: r = LHS(u) - RHS(f) = b - A u_I (float64), sums r.r and b.b, CG state init
 // ---------------------------------------------------------------------------------
 #ifndef EXCMG_RES_MINB
-#define EXCMG_RES_MINB 3  // 24 warps per SM (80 registers, a few spills): measured faster
+#define EXCMG_RES_MINB 3  // 24 warps per SM: measured faster than 16
 #endif
+
+// A residual tile: kTX columns along x (one warp) x kTY * kResRows rows along y (each
+// thread takes kResRows adjacent rows) x tz planes, covering nodes 0 .. n per direction.
+// (Tiles of the interior nodes 1 .. n, with the index-0 boundary nodes written by their
+// neighbours, hold no padding for power-of-two grids but measured 40% slower.)
+__device__ __forceinline__ TileXYZ res_tile_coords(const Grid3& g, const Tiling& tl, long long lt) {
+  TileXYZ c;
+  const int bx = (int)(lt % tl.ntx);
+  const long long r = lt / tl.ntx;
+  const int by = (int)(r % tl.nty);
+  const int bz = (int)(r / tl.nty);
+  c.x0 = bx * kTX;
+  c.y0 = by * kTY * kResRows;
+  c.z0 = bz * tl.tz;
+  c.z1 = min(c.z0 + tl.tz, g.nz + 1);
+  return c;
+}
+
+// The Dirichlet lift of node (i, j, k) next to an x or y boundary face: the part of its
+// 19-point sum over boundary nodes, grouped as the sum itself is (in-plane part of
+// plane k, plus the out-of-plane parts of planes k - 1 and k + 1, which are whole
+// boundary planes when k - 1 = 0 or k + 1 = nz).  Direct loads: about 3% of the nodes.
+__device__ double perim_lift(const double* __restrict__ u, const Grid3& g, const Coef& A, int i,
+                             int j, int k) {
+  const bool bxm = (i - 1 == 0), bxp = (i + 1 == g.nx), bym = (j - 1 == 0), byp = (j + 1 == g.ny);
+  auto at = [&](int x, int y, int z) { return __ldg(u + x + (long long)y * g.sy + (long long)z * g.sz); };
+  // out-of-plane part of plane kk: whole plane if it is a boundary plane, else its
+  // boundary columns
+  auto lt = [&](int kk) -> double {
+    if (kk == 0 || kk == g.nz) {
+      const double SX = at(i - 1, j, kk) + at(i + 1, j, kk), SY = at(i, j - 1, kk) + at(i, j + 1, kk);
+      return fma(A.fz, at(i, j, kk), fma(A.exz, SX, A.eyz * SY));
+    }
+    const double mSX = (bxm ? at(i - 1, j, kk) : 0.0) + (bxp ? at(i + 1, j, kk) : 0.0);
+    const double mSY = (bym ? at(i, j - 1, kk) : 0.0) + (byp ? at(i, j + 1, kk) : 0.0);
+    return fma(A.exz, mSX, A.eyz * mSY);
+  };
+  const double mSX = (bxm ? at(i - 1, j, k) : 0.0) + (bxp ? at(i + 1, j, k) : 0.0);
+  const double mSY = (bym ? at(i, j - 1, k) : 0.0) + (byp ? at(i, j + 1, k) : 0.0);
+  const double mEXY = ((bxm || bym) ? at(i - 1, j - 1, k) : 0.0) + ((bxp || bym) ? at(i + 1, j - 1, k) : 0.0) +
+                      ((bxm || byp) ? at(i - 1, j + 1, k) : 0.0) + ((bxp || byp) ? at(i + 1, j + 1, k) : 0.0);
+  const double LC = fma(A.fx, mSX, fma(A.fy, mSY, A.exy * mEXY));
+  return (LC + lt(k - 1)) + lt(k + 1);
+}
+
+// Each thread marches its kResRows rows of one x-column through the tile's planes.  Per
+// plane it loads the (kResRows + 2) x 3 neighbourhood (through the read-only cache:
+// neighbouring threads share the lines; no staging, no block barrier) and forms, per row,
+// the in-plane part C = c0 P + fx S_x + fy S_y + exy E_xy and the out-of-plane part
+// T = fz P + exz S_x + eyz S_y of the 19-point sum, with S_x = W + E computed once per
+// loaded row and shared by the rows above and below (E_xy of row j = S_x(j-1) + S_x(j+1),
+// the same grouping as (SW + SE) + (NW + NE)); the sum at plane k is C_k + T_{k-1} +
+// T_{k+1}.  The first and last plane of a tile contribute T only.  b (for ||b||) is
+// -RHS away from the boundary; next to a z-boundary plane its lift is that plane's T;
+// next to an x or y boundary face it is formed by perim_lift.
 template <typename TR>
 __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
     k_residual(int nprob, const ResDesc* __restrict__ descs, long long total_tiles,
                CGState* st, double* partials, unsigned* counters) {
+  constexpr int R = kResRows;
   __shared__ int s_active[kMaxProb];
   __shared__ double s_part[2 * kMaxProb];
   for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
@@ -706,94 +762,75 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
     const Grid3 g = d.g;
     const double* __restrict__ u = d.u;
     TR* __restrict__ rout = reinterpret_cast<TR*>(d.r);
-    const TileXYZ c = tile_coords(g, d.t, t - d.tile_begin);
-    const int i = c.x0 + tx, j = c.y0 + ty;
-    const bool own = (i <= g.nx) && (j <= g.ny);
-    const bool inxy = (i > 0) && (i < g.nx) && (j > 0) && (j < g.ny);
-    // interior columns next to an x or y boundary face: their lift has in-plane terms
-    const bool perim = inxy && (i == 1 || i == g.nx - 1 || j == 1 || j == g.ny - 1);
-    // which of the 3x3 neighbour columns are boundary columns
-    const bool bxm = (i - 1 == 0), bxp = (i + 1 == g.nx), bym = (j - 1 == 0), byp = (j + 1 == g.ny);
-    const bool deep = inxy && !perim;  // no boundary node in this column's 3x3 neighbourhood
+    const TileXYZ c = res_tile_coords(g, d.t, t - d.tile_begin);
+    const int i = c.x0 + tx, jb = c.y0 + R * ty;  // rows jb .. jb + R - 1
+    const bool colx = (i > 0) && (i < g.nx);
     const bool want_b = d.want_b != 0;
-    const Coef A = d.A;
-    // C/T terms (see k_dir_spmv_dot) of the stencil of u over all 19 nodes, and of its
-    // boundary part: b = LHS(boundary part of u) - RHS(f)
-    double Cm1 = 0, Tm1 = 0, Tm2 = 0, LCm1 = 0, LTm1 = 0, LTm2 = 0;
     const bool use_f = d.src == nullptr;
-    // the 3x3 neighbourhood of column (i, j) in plane kk, read through the read-only
-    // cache (neighbouring threads share the lines): no staging and no block barrier
-    auto load_n = [&](int kk, double* v) {
+    const Coef A = d.A;
+    double Cm1[R], Tm1[R], Tm2[R];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) v[q] = 0.0;
-      if (kk < 0 || kk > g.nz) return;
+    for (int q = 0; q < R; ++q) Cm1[q] = Tm1[q] = Tm2[q] = 0.0;
+    for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
+      const bool need_c = (kk >= c.z0) && (kk < c.z1);  // C of the tile's own planes only
+      // the neighbourhood: rows jb - 1 .. jb + R (index y = row - jb + 1), columns i - 1,
+      // i, i + 1; zero outside the grid
+      double Pv[R + 2], SXv[R + 2];
+      const bool kin = kk >= 0 && kk <= g.nz;
       const double* pl = u + (long long)kk * g.sz;
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const int gi = i + (q % 3) - 1, gj = j + (q / 3) - 1;
-        if (gi >= 0 && gi <= g.nx && gj >= 0 && gj <= g.ny) v[q] = __ldg(pl + gi + gj * g.sy);
+      for (int y = 0; y < R + 2; ++y) {
+        const int gj = jb - 1 + y;
+        const bool rin = kin && gj >= 0 && gj <= g.ny;
+        const double* row = pl + (long long)gj * g.sy;
+        const double W = (rin && i - 1 >= 0 && i - 1 <= g.nx) ? __ldg(row + i - 1) : 0.0;
+        const double E = (rin && i + 1 <= g.nx) ? __ldg(row + i + 1) : 0.0;
+        Pv[y] = (rin && i <= g.nx) ? __ldg(row + i) : 0.0;
+        SXv[y] = W + E;
       }
-    };
-    // (no software prefetch: without block barriers the warps march independently and
-    // hide each other's load latency)
-    for (int kk = c.z0 - 1; kk <= c.z1; ++kk) {
-      const bool plane_bnd = (kk == 0) || (kk == g.nz);
-      double nb[9];
-      load_n(kk, nb);
-      const double SW = nb[0], S = nb[1], SE = nb[2], W = nb[3], P = nb[4], E = nb[5];
-      const double NW = nb[6], N = nb[7], NE = nb[8];
-      const double SX = W + E, SY = S + N, EXY = (SW + SE) + (NW + NE);
-      const double Ck = fma(A.c0, P, fma(A.fx, SX, fma(A.fy, SY, A.exy * EXY)));
-      const double Tk = fma(A.fz, P, fma(A.exz, SX, A.eyz * SY));
-      double LCk = 0.0, LTk = 0.0;
-      if (want_b) {
-        if (plane_bnd) {  // every node of a z-boundary plane is a boundary node
-          LCk = Ck;
-          LTk = Tk;
-        } else if (perim) {  // only the boundary columns of this plane
-          const double mSX = (bxm ? W : 0.0) + (bxp ? E : 0.0);
-          const double mSY = (bym ? S : 0.0) + (byp ? N : 0.0);
-          const double mEXY = ((bxm || bym) ? SW : 0.0) + ((bxp || bym) ? SE : 0.0) +
-                              ((bxm || byp) ? NW : 0.0) + ((bxp || byp) ? NE : 0.0);
-          LCk = fma(A.fx, mSX, fma(A.fy, mSY, A.exy * mEXY));
-          LTk = fma(A.exz, mSX, A.eyz * mSY);
-        }
-      }
-      const int kc = kk - 1;
-      if (kc >= c.z0 && own) {
-        const long long o = i + j * g.sy + (long long)kc * g.sz;
-        double rv = 0.0;
-        if (inxy && kc > 0 && kc < g.nz) {
-          // twice the right-hand side of eq. (compact), 6 f_c + the 6 face values of f (the
-          // face values are re-read through L1 by the neighbouring threads); the factor
-          // 1/2 is applied inside the fused multiply-adds below, exactly
-          const View& F = d.f;
-          const double rhs2 =
-              use_f ? fma(6.0, F.at(i, j, kc), ((F.at(i - 1, j, kc) + F.at(i + 1, j, kc)) +
-                                                (F.at(i, j - 1, kc) + F.at(i, j + 1, kc)) +
-                                                (F.at(i, j, kc - 1) + F.at(i, j, kc + 1))))
-                    : -2.0 * d.src[o];
-          if (d.rhs_out) d.rhs_out[o] = -0.5 * rhs2;
-          // LHS(u) - RHS = -(A-stencil of u over all 19 nodes) - RHS
-          rv = fma(-0.5, rhs2, -((Cm1 + Tm2) + Tk));
-          acc_r = fma(rv, rv, acc_r);
-          if (want_b) {
-            if (deep && kc >= 2 && kc <= g.nz - 2) {
-              acc_b4 = fma(rhs2, rhs2, acc_b4);  // b = -RHS here
-            } else {
-              const double bv = fma(-0.5, rhs2, -((LCm1 + LTm2) + LTk));
-              acc_b = fma(bv, bv, acc_b);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int y = q + 1, j = jb + q;
+        const double SX = SXv[y], SY = Pv[y - 1] + Pv[y + 1], P = Pv[y];
+        double Ck = 0.0;
+        if (need_c) Ck = fma(A.c0, P, fma(A.fx, SX, fma(A.fy, SY, A.exy * (SXv[y - 1] + SXv[y + 1]))));
+        const double Tk = fma(A.fz, P, fma(A.exz, SX, A.eyz * SY));
+        const int kc = kk - 1;
+        if (kc >= c.z0 && i <= g.nx && j <= g.ny) {
+          const long long o = i + j * g.sy + (long long)kc * g.sz;
+          double rv = 0.0;
+          if (colx && j > 0 && j < g.ny && kc > 0 && kc < g.nz) {
+            // twice the right-hand side of eq. (compact), 6 f_c + the 6 face values of f
+            // (the face values are re-read through L1 by the neighbouring threads); the
+            // factor 1/2 is applied inside the fused multiply-adds below, exactly
+            const View& F = d.f;
+            const double rhs2 =
+                use_f ? fma(6.0, F.at(i, j, kc), ((F.at(i - 1, j, kc) + F.at(i + 1, j, kc)) +
+                                                  (F.at(i, j - 1, kc) + F.at(i, j + 1, kc)) +
+                                                  (F.at(i, j, kc - 1) + F.at(i, j, kc + 1))))
+                      : -2.0 * d.src[o];
+            if (d.rhs_out) d.rhs_out[o] = -0.5 * rhs2;
+            // LHS(u) - RHS = -(A-stencil of u over all 19 nodes) - RHS
+            rv = fma(-0.5, rhs2, -((Cm1[q] + Tm2[q]) + Tk));
+            acc_r = fma(rv, rv, acc_r);
+            if (want_b) {
+              const bool perim = (i == 1 || i == g.nx - 1 || j == 1 || j == g.ny - 1);
+              if (!perim && kc >= 2 && kc <= g.nz - 2) {
+                acc_b4 = fma(rhs2, rhs2, acc_b4);  // b = -RHS here
+              } else {
+                const double lift = perim ? perim_lift(u, g, A, i, j, kc)
+                                          : (kc == 1 ? Tm2[q] : 0.0) + (kc == g.nz - 1 ? Tk : 0.0);
+                const double bv = fma(-0.5, rhs2, -lift);
+                acc_b = fma(bv, bv, acc_b);
+              }
             }
           }
+          rout[o] = (TR)rv;
         }
-        rout[o] = (TR)rv;
+        Tm2[q] = Tm1[q];
+        Tm1[q] = Tk;
+        Cm1[q] = Ck;
       }
-      Tm2 = Tm1;
-      Tm1 = Tk;
-      Cm1 = Ck;
-      LTm2 = LTm1;
-      LTm1 = LTk;
-      LCm1 = LCk;
     }
   }
   if (cur >= 0) {
@@ -900,6 +937,23 @@ int persistent_grid(long long total_tiles) {
     if (g_max_grid > kMaxGrid) g_max_grid = kMaxGrid;
   }
   long long g = total_tiles < g_max_grid ? total_tiles : g_max_grid;
+  return g < 1 ? 1 : (int)g;
+}
+
+static int g_res_grid = 0;
+
+int residual_grid(long long total_tiles) {
+  if (g_res_grid == 0) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual<double>, kThreads, 0);
+    if (sms <= 0) sms = 1;
+    if (occ <= 0) occ = 1;
+    g_res_grid = sms * occ;
+    if (g_res_grid > kMaxGrid) g_res_grid = kMaxGrid;
+  }
+  long long g = total_tiles < g_res_grid ? total_tiles : g_res_grid;
   return g < 1 ? 1 : (int)g;
 }
 

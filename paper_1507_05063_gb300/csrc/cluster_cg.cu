@@ -92,12 +92,20 @@ __device__ double2 cluster_sum2(double a, double b, double* s_park, double* slot
   s_park[32 * NW + threadIdx.x] = b;
   __syncthreads();
   if (warp == 0) {
-    double ta = 0.0, tb = 0.0;
+    double va[NW], vb[NW];
 #pragma unroll
     for (int u = 0; u < NW; ++u) {
-      ta += s_park[lane + 32 * u];
-      tb += s_park[32 * NW + lane + 32 * u];
+      va[u] = s_park[lane + 32 * u];
+      vb[u] = s_park[32 * NW + lane + 32 * u];
     }
+#pragma unroll
+    for (int w = 1; w < NW; w *= 2)  // pairwise: a dependence chain of log2(NW) adds
+#pragma unroll
+      for (int u = 0; u + w < NW; u += 2 * w) {
+        va[u] += va[u + w];
+        vb[u] += vb[u + w];
+      }
+    double ta = va[0], tb = vb[0];
     // a full butterfly: every lane holds the CTA's sums (lane c stores into CTA c, and
     // the cluster may have more CTAs than this CTA has warps -- a CTA given a wrong
     // partial would take other decisions than its peers)
@@ -117,8 +125,12 @@ __device__ double2 cluster_sum2(double a, double b, double* s_park, double* slot
   if (warp == 0) {
     double ta = lane < csize ? slots[lane] : 0.0;
     double tb = lane < csize ? slots[kClMax + lane] : 0.0;
-    ta = xor_sum(ta, kClMax / 2);  // fixed order: identical in every CTA
-    tb = xor_sum(tb, kClMax / 2);
+    // a butterfly over the smallest power of two >= csize lanes: fixed order (csize is
+    // the same in every CTA), so identical in every CTA
+    int from = 1;
+    while (from < csize) from <<= 1;
+    ta = xor_sum(ta, from >> 1);
+    tb = xor_sum(tb, from >> 1);
     t.x = __shfl_sync(0xffffffffu, ta, 0);
     t.y = __shfl_sync(0xffffffffu, tb, 0);
   }

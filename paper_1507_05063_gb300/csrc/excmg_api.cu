@@ -47,6 +47,12 @@ Tiling make_tiling(const Grid3& g, int tz) {
   return t;
 }
 
+Tiling make_res_tiling(const Grid3& g, int tz) {
+  Tiling t = make_tiling(g, tz);
+  t.nty = (g.ny + 1 + kTY * kResRows - 1) / (kTY * kResRows);
+  return t;
+}
+
 
 // Slab depth: among 1..64 the one minimising (waves of tiles) x (planes staged per tile),
 // a model of the stencil kernel's time when every block runs at the same rate.  Large
@@ -522,7 +528,7 @@ ResDesc make_res(const Grid3& g, const Tiling& t, int slot, const double* x, Vie
   memset(&r, 0, sizeof(r));
   r.g = g;
   r.A = make_coef(g);
-  r.t = t;
+  r.t = make_res_tiling(g, t.tz);
   r.slot = slot;
   r.u = x;
   r.f = f;
@@ -566,17 +572,18 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
   const int n = (int)items.size();
   std::vector<CGState> hs;
   std::vector<ResDesc> hr;
-  long long tiles = 0;
+  long long tiles = 0, rtiles = 0;  // CG tiles, residual tiles
   for (int a = 0; a < n; ++a) {
     Item& it = items[a];
     it.iters = it.refs = 0;
     it.status = EXCMG_OK;
     it.relres = 0.0;
     ResDesc r = it.res;
-    r.tile_begin = tiles;
+    r.tile_begin = rtiles;
+    rtiles += r.t.count();
     it.d64.tile_begin = tiles;
     it.d32.tile_begin = tiles;
-    tiles += r.t.count();
+    tiles += it.d64.t.count();
     if (mixed) {
       r.r = it.d32.r;
       // the inner solve stops at inner_tol x its starting residual, or as soon as its
@@ -610,7 +617,8 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     CK(cudaMemcpyAsync(c.resd(), hr.data(), sizeof(ResDesc) * n, cudaMemcpyHostToDevice, c.s));
     CK(cudaMemcpyAsync(c.cgd(), hd.data(), sizeof(CGDesc<double>) * n, cudaMemcpyHostToDevice, c.s));
     CK(c.timed(EXCMG_K_RESIDUAL, nodes_sum, [&] {
-      return launch_residual(false, n, c.resd(), tiles, grid, c.st(), c.partials(), c.counters(), c.s);
+      return launch_residual(false, n, c.resd(), rtiles, residual_grid(rtiles), c.st(), c.partials(),
+                             c.counters(), c.s);
     }));
     // DSOLVE levels: one direct solve each (their states are done with 0 steps, so the
     // CG engines skip them)
@@ -667,7 +675,7 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     for (int a : cur) rnodes += (double)items[a].nodes;
     CK(cudaMemcpyAsync(c.resd(), rr.data(), sizeof(ResDesc) * nr, cudaMemcpyHostToDevice, c.s));
     CK(c.timed(EXCMG_K_RESIDUAL, rnodes, [&] {
-      return launch_residual(true, nr, c.resd(), rt, tiles_grid(rt), c.st(), c.partials(), c.counters(), c.s);
+      return launch_residual(true, nr, c.resd(), rt, residual_grid(rt), c.st(), c.partials(), c.counters(), c.s);
     }));
     excmg_status e = read_states(c, nslots, hs);
     if (e != EXCMG_OK) return e;
@@ -1171,8 +1179,8 @@ excmg_status excmg_residual(const excmg_grid* grid, const double* f, const doubl
   d.r = r;
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
   CK(cudaMemcpyAsync(c.resd(), &d, sizeof(d), cudaMemcpyHostToDevice, c.s));
-  CK(launch_residual(false, 1, c.resd(), t.count(), persistent_grid(t.count()), c.st(), c.partials(),
-                     c.counters(), c.s));
+  CK(launch_residual(false, 1, c.resd(), d.t.count(), residual_grid(d.t.count()), c.st(),
+                     c.partials(), c.counters(), c.s));
   std::vector<CGState> hs;
   excmg_status e = read_states(c, 1, hs);
   if (e != EXCMG_OK) return e;

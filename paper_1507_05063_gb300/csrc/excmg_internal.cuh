@@ -18,6 +18,10 @@ constexpr int kMaxProb = 128;    // problems per batched launch
 constexpr int kThreads = 256;    // threads of every tiled kernel
 constexpr int kTX = 32;          // x-width of a stencil tile (one warp)
 constexpr int kTY = 8;           // y-rows of a stencil tile
+#ifndef EXCMG_RES_ROWS
+#define EXCMG_RES_ROWS 1  // 2 and 4 measured slower
+#endif
+constexpr int kResRows = EXCMG_RES_ROWS;  // y-rows per thread of the residual kernel
 constexpr int kMaxGrid = 4096;   // cap on persistent grid size (partials per problem)
 #ifndef EXCMG_CLUSTER_MAX_NODES
 #define EXCMG_CLUSTER_MAX_NODES 20000
@@ -82,6 +86,8 @@ struct Tiling {
   __host__ __device__ long long count() const { return (long long)ntx * nty * ntz; }
 };
 Tiling make_tiling(const Grid3& g, int tz);
+// The residual kernel's tiling: kTY * kResRows rows per tile, the same x-width and tz.
+Tiling make_res_tiling(const Grid3& g, int tz);
 int choose_tz(const Grid3& g, int grid_blocks, int requested);
 
 // One problem of a CG phase.
@@ -147,6 +153,8 @@ cudaError_t launch_add_correction(int nprob, const CGDesc<float>* inner, long lo
 cudaError_t launch_scale_rhs(int nprob, const CGDesc<float>* inner, long long total_tiles,
                              int grid, CGState* st, cudaStream_t s);
 int persistent_grid(long long total_tiles);
+// Blocks of a residual launch: all co-resident blocks of k_residual, at most one per tile.
+int residual_grid(long long total_tiles);
 
 // All CG steps of every problem of `descs` in one cooperative launch.  Problem p owns
 // the blocks [blk_begin, blk_begin + blk_count) and iterates independently of the

@@ -119,7 +119,7 @@ extern "C" excmg_status excmg_cg_noalloc(const excmg_grid* grid, const double* f
   memset(&rd, 0, sizeof(rd));
   rd.g = g;
   rd.A = make_coef(g);
-  rd.t = t;
+  rd.t = make_res_tiling(g, t.tz);
   rd.slot = 0;
   rd.u = u;
   rd.f = View{f, 1, g.sy, g.sz};
@@ -149,7 +149,8 @@ extern "C" excmg_status excmg_cg_noalloc(const excmg_grid* grid, const double* f
   CKN(cudaMemcpyAsync(base + L.cgd, &cd, sizeof(cd), cudaMemcpyHostToDevice, s));
   const ResDesc* drd = reinterpret_cast<const ResDesc*>(base + L.resd);
   const CGDesc<double>* dcd = reinterpret_cast<const CGDesc<double>*>(base + L.cgd);
-  CKN(launch_residual(false, 1, drd, t.count(), nblk, st, partials, counters, s));
+  CKN(launch_residual(false, 1, drd, rd.t.count(), residual_grid(rd.t.count()), st, partials,
+                      counters, s));
   long long launches = 1;
   CGState hs;
   int chunk = opt->chunk > 0 ? opt->chunk : 4;

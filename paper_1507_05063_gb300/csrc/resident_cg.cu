@@ -46,22 +46,34 @@ __device__ __forceinline__ double rs_xor_sum(double v, int from) {
   return v;
 }
 
-// Block sums of (a, b): every thread parks its values in shared memory and warp 0 adds
-// them (kRsThreads / 32 per lane, then a butterfly) -- a handful of float64 warp
-// instructions instead of a butterfly in every warp.  Sums valid in warp 0.
-__device__ double2 rs_block_sum2(double a, double b, double* s_park) {
-  s_park[threadIdx.x] = a;
-  s_park[kRsThreads + threadIdx.x] = b;
+// Block sums of (a, b) over the first nw warps (the warps that own nodes; the others
+// hold zeros): those threads park their values in shared memory and warp 0 adds them
+// (nw per lane as a pairwise tree, then a butterfly) -- a handful of float64 warp
+// instructions on a short dependence chain instead of a butterfly in every warp.
+// nw is the same in every block.  Sums valid in warp 0.
+__device__ double2 rs_block_sum2(double a, double b, double* s_park, int nw) {
+  if (threadIdx.x < 32 * nw) {
+    s_park[threadIdx.x] = a;
+    s_park[kRsThreads + threadIdx.x] = b;
+  }
   __syncthreads();
   double2 t = make_double2(0.0, 0.0);
   if (threadIdx.x < 32) {
-    double ta = 0.0, tb = 0.0;
+    double va[kRsThreads / 32], vb[kRsThreads / 32];
 #pragma unroll
     for (int u = 0; u < kRsThreads / 32; ++u) {
-      ta += s_park[threadIdx.x + 32 * u];
-      tb += s_park[kRsThreads + threadIdx.x + 32 * u];
+      va[u] = u < nw ? s_park[threadIdx.x + 32 * u] : 0.0;
+      vb[u] = u < nw ? s_park[kRsThreads + threadIdx.x + 32 * u] : 0.0;
     }
-    t = make_double2(rs_xor_sum(ta, 16), rs_xor_sum(tb, 16));
+#pragma unroll
+    for (int w = 1; w < kRsThreads / 32; w *= 2)
+#pragma unroll
+      for (int u = 0; u + w < kRsThreads / 32; u += 2 * w)
+        if (u + w < nw) {
+          va[u] += va[u + w];
+          vb[u] += vb[u + w];
+        }
+    t = make_double2(rs_xor_sum(va[0], 16), rs_xor_sum(vb[0], 16));
   }
   return t;
 }
@@ -144,6 +156,7 @@ __global__ void __launch_bounds__(kRsThreads)
   const int BX = D.bx, BY = D.by, BZ = D.bz;
   const int EX = BX + 2, EY = BY + 2, EZ = BZ + 2;
   const int B = BX * BY * BZ, ext = EX * EY * EZ;
+  const int nw_own = min(kRsThreads, B + 31) / 32;  // warps that own nodes
   const int b = blockIdx.x;
   const int ibx = b % D.nbx, iby = (b / D.nbx) % D.nby, ibz = b / (D.nbx * D.nby);
   // global node of box-local (0, 0, 0); the halo starts one node before
@@ -265,7 +278,7 @@ __global__ void __launch_bounds__(kRsThreads)
   };
   unsigned seq = 1;
   {
-    const double2 part = rs_block_sum2(0.0, acc_d, s_park);
+    const double2 part = rs_block_sum2(0.0, acc_d, s_park, nw_own);
     const bool ok = rs_arrive_wait(part, pairs, counter, G, seq, err, &s_ok);
     if (ok) load_halo(0);
     if (threadIdx.x < 32) {
@@ -352,7 +365,7 @@ __global__ void __launch_bounds__(kRsThreads)
     }
     // 4. the grid reduction (it also orders every block's publications before the next
     // step's halo loads); the next halo's loads; scalars
-    const double2 part = rs_block_sum2(acc_g, acc_d, s_park);
+    const double2 part = rs_block_sum2(acc_g, acc_d, s_park, nw_own);
     const bool ok = rs_arrive_wait(part, pairs, counter, G, seq, err, &s_ok);
     par ^= 1;
     if (ok) load_halo(par);
