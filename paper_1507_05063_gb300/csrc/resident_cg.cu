@@ -47,10 +47,12 @@ __device__ __forceinline__ double rs_xor_sum(double v, int from) {
 }
 
 // Block sums of (a, b) over the first nw warps (the warps that own nodes; the others
-// hold zeros): those threads park their values in shared memory and warp 0 adds them
-// (nw per lane as a pairwise tree, then a butterfly) -- a handful of float64 warp
-// instructions on a short dependence chain instead of a butterfly in every warp.
-// nw is the same in every block.  Sums valid in warp 0.
+// hold zeros), valid in every lane of warp 0.  Those threads park their values in shared
+// memory; warp 0 adds them with a and b packed into the two half-warps (lanes 0-15 the
+// a-values, lanes 16-31 the b-values: 2 nw values per lane as a pairwise tree, then a
+// butterfly over 16 lanes), so each level of the dependence chain is one float64 warp
+// instruction for both sums.  On GB300 every float64 warp instruction costs the narrow
+// FP64 pipe the same whether it carries one sum or two.  nw is the same in every block.
 __device__ double2 rs_block_sum2(double a, double b, double* s_park, int nw) {
   if (threadIdx.x < 32 * nw) {
     s_park[threadIdx.x] = a;
@@ -59,21 +61,19 @@ __device__ double2 rs_block_sum2(double a, double b, double* s_park, int nw) {
   __syncthreads();
   double2 t = make_double2(0.0, 0.0);
   if (threadIdx.x < 32) {
-    double va[kRsThreads / 32], vb[kRsThreads / 32];
+    const int lane = threadIdx.x, h = lane & 15;
+    const double* src = s_park + (lane < 16 ? 0 : kRsThreads);
+    const int nv = 2 * nw;  // values per lane
+    double v[kRsThreads / 16];
 #pragma unroll
-    for (int u = 0; u < kRsThreads / 32; ++u) {
-      va[u] = u < nw ? s_park[threadIdx.x + 32 * u] : 0.0;
-      vb[u] = u < nw ? s_park[kRsThreads + threadIdx.x + 32 * u] : 0.0;
-    }
+    for (int u = 0; u < kRsThreads / 16; ++u) v[u] = u < nv ? src[h + 16 * u] : 0.0;
 #pragma unroll
-    for (int w = 1; w < kRsThreads / 32; w *= 2)
+    for (int w = 1; w < kRsThreads / 16; w *= 2)
 #pragma unroll
-      for (int u = 0; u + w < kRsThreads / 32; u += 2 * w)
-        if (u + w < nw) {
-          va[u] += va[u + w];
-          vb[u] += vb[u + w];
-        }
-    t = make_double2(rs_xor_sum(va[0], 16), rs_xor_sum(vb[0], 16));
+      for (int u = 0; u + w < kRsThreads / 16; u += 2 * w)
+        if (u + w < nv) v[u] += v[u + w];
+    const double r = rs_xor_sum(v[0], 8);
+    t = make_double2(__shfl_sync(0xffffffffu, r, 0), __shfl_sync(0xffffffffu, r, 16));
   }
   return t;
 }
@@ -106,39 +106,49 @@ __device__ bool rs_arrive_wait(double2 part, double2* pairs, unsigned* counter, 
   return *s_ok != 0;
 }
 
-// Warp 0, after the wait: the sums of the G pairs of set seq & 1, in a fixed order (lane
-// l takes pairs l, l + 32, ...: kRsPB loads in flight, a tree within the lane, then a
-// butterfly), identical in every lane and every block.
+// Warp 0, after the wait: the sums of the G pairs of set seq & 1, in a fixed order,
+// identical in every lane and every block.  As in rs_block_sum2 the two sums share the
+// warp: lanes 0-15 take the first members of pairs h, h + 16, ... (h = lane mod 16),
+// lanes 16-31 the second members (kRsPB loads in flight, a tree within the lane), then a
+// butterfly over 16 lanes.
 __device__ double2 rs_read_pairs(const double2* pairs, int G, unsigned seq) {
-  const double2* set = pairs + (size_t)(seq & 1) * G;
-  const int lane = threadIdx.x & 31;
-  double sa = 0.0, sb = 0.0;
-  for (int i0 = 0; i0 < G; i0 += 32 * kRsPB) {
-    double2 v[kRsPB];
+  const double* set = reinterpret_cast<const double*>(pairs + (size_t)(seq & 1) * G);
+  const int lane = threadIdx.x & 31, h = lane & 15, m = lane >> 4;
+  double acc = 0.0;
+  for (int i0 = 0; i0 < G; i0 += 16 * kRsPB) {
+    const int nv = min(kRsPB, (G - i0 + 15) / 16);  // values per lane in this chunk
+    double v[kRsPB];
 #pragma unroll
     for (int u = 0; u < kRsPB; ++u) {
-      const int i = i0 + lane + 32 * u;
-      v[u] = i < G ? __ldcg(&set[i]) : make_double2(0.0, 0.0);
+      const int i = i0 + h + 16 * u;
+      v[u] = i < G ? __ldcg(set + 2 * i + m) : 0.0;
     }
 #pragma unroll
     for (int w = 1; w < kRsPB; w *= 2)
 #pragma unroll
-      for (int u = 0; u + w < kRsPB; u += 2 * w) {
-        v[u].x += v[u + w].x;
-        v[u].y += v[u + w].y;
-      }
-    sa += v[0].x;
-    sb += v[0].y;
+      for (int u = 0; u + w < kRsPB; u += 2 * w)
+        if (u + w < nv) v[u] += v[u + w];
+    acc += v[0];
   }
-  return make_double2(rs_xor_sum(sa, 16), rs_xor_sum(sb, 16));
+  const double r = rs_xor_sum(acc, 8);
+  return make_double2(__shfl_sync(0xffffffffu, r, 0), __shfl_sync(0xffffffffu, r, 16));
 }
 
-// 19-point A-stencil at offset 0 of P with strides (1, ey, ez).
-__device__ __forceinline__ double rs_stencil(const double* P, int ey, int ez, const Coef& A) {
+// 19-point A-stencil at offset 0 of P with strides (1, ey, ez).  `shallow`: the seven
+// weighted terms as a tree (two more float64 instructions, three fewer levels of
+// dependence) -- for boxes of at most one node per thread, where a step waits on the
+// chain rather than on the FP64 pipe's throughput.
+__device__ __forceinline__ double rs_stencil(const double* P, int ey, int ez, const Coef& A,
+                                             bool shallow) {
   const double SX = P[-1] + P[1], SY = P[-ey] + P[ey], SZ = P[-ez] + P[ez];
   const double EXY = (P[-1 - ey] + P[1 - ey]) + (P[-1 + ey] + P[1 + ey]);
   const double EXZ = (P[-1 - ez] + P[1 - ez]) + (P[-1 + ez] + P[1 + ez]);
   const double EYZ = (P[-ey - ez] + P[ey - ez]) + (P[-ey + ez] + P[ey + ez]);
+  if (shallow) {
+    const double t1 = fma(A.c0, P[0], A.fx * SX), t2 = fma(A.fy, SY, A.fz * SZ);
+    const double t3 = fma(A.exy, EXY, A.exz * EXZ);
+    return (t1 + t2) + fma(A.eyz, EYZ, t3);
+  }
   return fma(A.c0, P[0], fma(A.fx, SX, fma(A.fy, SY, fma(A.fz, SZ, fma(A.exy, EXY, fma(A.exz, EXZ, A.eyz * EYZ))))));
 }
 
@@ -157,6 +167,7 @@ __global__ void __launch_bounds__(kRsThreads)
   const int EX = BX + 2, EY = BY + 2, EZ = BZ + 2;
   const int B = BX * BY * BZ, ext = EX * EY * EZ;
   const int nw_own = min(kRsThreads, B + 31) / 32;  // warps that own nodes
+  const bool shallow = B <= kRsThreads;               // at most one node per thread
   const int b = blockIdx.x;
   const int ibx = b % D.nbx, iby = (b / D.nbx) % D.nby, ibz = b / (D.nbx * D.nby);
   // global node of box-local (0, 0, 0); the halo starts one node before
@@ -236,7 +247,7 @@ __global__ void __launch_bounds__(kRsThreads)
     const Own n = own_node(q);
     double w = 0.0;
     if (n.valid) {
-      w = rs_stencil(R + n.e, EX, EX * EY, A);
+      w = rs_stencil(R + n.e, EX, EX * EY, A, shallow);
       acc_d = fma(w, R[n.e], acc_d);
       D.w0[n.o] = w;
       D.s0[n.o] = 0.0;
@@ -356,7 +367,7 @@ __global__ void __launch_bounds__(kRsThreads)
       double w = 0.0;
       if (n.valid) {
         const double r = R[n.e];
-        w = rs_stencil(R + n.e, EX, EX * EY, A);
+        w = rs_stencil(R + n.e, EX, EX * EY, A, shallow);
         acc_g = fma(r, r, acc_g);
         acc_d = fma(w, r, acc_d);
         __stcg(Wn + n.o, w);
