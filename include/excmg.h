@@ -114,6 +114,15 @@ typedef struct {
                               or 0: the uniform eps of Algorithm 1 */
   int prolong;             /* excmg_prolong: how the initial guess w_h of levels >= 2 is
                               formed (Algorithm 1, line 6); default QUARTIC */
+  double* history;         /* HOST array or NULL: the residual history of the finest
+                              level (the relative residual against the CG step, as in the
+                              figure of Section 5 that plots it): history[k] =
+                              ||r_k||_2 / ||b||_2 after k steps, r_k CG's recursively
+                              updated residual (the one the stopping test reads), for
+                              k = 0 .. min(iters, history_len - 1); later entries are left
+                              unchanged.  excmg_solve and excmg_cg (its one level), FP64
+                              only; the workspace grows by history_len doubles */
+  int history_len;         /* entries of `history` (>= 1 when history is set) */
 } excmg_options;
 
 /* DSOLVE of Algorithm 1 (levels 0 and 1).  DIRECT: the exact discrete solution by the

@@ -523,7 +523,8 @@ def level_sizes(N, N0):
 
 
 def excmg(f, g, L, N, N0, eps, eps_coarse=1e-12, max_iter=100000, dsolve="cg",
-          fixed_iters=None, want_utilde=True, eps_ratio=1.0, prolong_kind="quartic"):
+          fixed_iters=None, want_utilde=True, eps_ratio=1.0, prolong_kind="quartic",
+          history=None):
     """EXCMG(A_h, f_h, L, eps) of Algorithm 1.
 
     ``f``, ``g``: finest-grid node arrays (g read on boundary nodes only).  ``L``: box
@@ -535,7 +536,9 @@ def excmg(f, g, L, N, N0, eps, eps_coarse=1e-12, max_iter=100000, dsolve="cg",
     uniform eps of Algorithm 1 when r = 1; r = 2**6 follows the sixth-order error of
     the extrapolated solution from level to level, Section 5's remark on uniform eps).
     ``prolong_kind``: 'quartic' (EXP_finite, the method), or the comparison
-    prolongations 'quadratic' / 'linear' (``prolong``).
+    prolongations 'quadratic' / 'linear' (``prolong``).  ``history``: a list that
+    receives the finest level's relative residual before each CG step and after the
+    last (the curve of the residual-history figure of Section 5).
     Returns a dict of per-level lists: 'u', 'w', 'ut', 'iters', 'relres', 'h', 'N'.
     """
     sizes = level_sizes(N, N0)
@@ -558,7 +561,8 @@ def excmg(f, g, L, N, N0, eps, eps_coarse=1e-12, max_iter=100000, dsolve="cg",
         else:
             w = prolong(prolong_kind, out["u"][l - 1], out["u"][l - 2])
             eps_l = eps * eps_ratio ** (len(sizes) - 1 - l)
-            ul, it, rel = cg(with_boundary(w, gl), fl, hl, eps_l, max_iter, fixed)
+            hist = history if l == len(sizes) - 1 else None
+            ul, it, rel = cg(with_boundary(w, gl), fl, hl, eps_l, max_iter, fixed, history=hist)
         out["u"].append(ul)
         out["w"].append(w)
         out["iters"].append(it)

@@ -152,6 +152,8 @@ struct FinBeta {
     S.rr = rr;
     S.iter += 1;
     S.first = 0;
+    const CGDesc<T>& d = descs[p];
+    if (d.hist && S.iter < d.hist_len) d.hist[S.iter] = rr;
     if (!isfinite(rr)) {
       S.status = EXCMG_ERR_NONFINITE;
       S.done = 1;
@@ -184,6 +186,7 @@ struct FinRes {
     S.fixed = d.fixed;
     S.status = EXCMG_OK;
     S.tol2 = d.fixed ? -1.0 : fmax(d.tol_b2 * bb, d.tol_r2 * rr);
+    if (d.hist && d.hist_len > 0) d.hist[0] = rr;
     S.done = d.fixed ? (d.max_iter <= 0) : (rr <= S.tol2 || d.max_iter <= 0);
     if (!isfinite(rr) || !isfinite(bb)) {
       S.status = EXCMG_ERR_NONFINITE;
@@ -613,6 +616,7 @@ __device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* 
     rr = rrn;
     iter += 1;
     first = false;
+    if (bl == 0 && threadIdx.x == 0 && d.hist && iter < d.hist_len) d.hist[iter] = rr;
     if (!isfinite(rr)) {
       status = EXCMG_ERR_NONFINITE;
       break;

@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(NT)
     if (warp == 0) {
       const double gn = red.x, dn = red.y;
       iter += 1;
+      if (me == 0 && lane == 0 && d.hist && iter < d.hist_len) d.hist[iter] = gn;
       int st_ = 0;
       if (!isfinite(gn) || !isfinite(dn)) {
         status = EXCMG_ERR_NONFINITE;

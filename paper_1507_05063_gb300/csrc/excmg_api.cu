@@ -133,6 +133,7 @@ bool options_ok(const excmg_options* o) {
   if (o->prolong != EXCMG_PROLONG_QUARTIC && o->prolong != EXCMG_PROLONG_QUADRATIC &&
       o->prolong != EXCMG_PROLONG_LINEAR)
     return false;
+  if (o->history && (o->history_len < 1 || o->precision != EXCMG_FP64)) return false;
   return true;
 }
 
@@ -313,6 +314,7 @@ struct Ctx {
   char* ws;
   Header H;
   cudaStream_t s;
+  double* hist = nullptr;         // device r.r history of the finest level (options.history)
   long long* launches = nullptr;  // kernels launched by this call
   Prof* prof = nullptr;           // set when the call is profiled
   bool persistent_ok = false;     // single-problem CG may use the cooperative kernel
@@ -339,6 +341,22 @@ struct Ctx {
   ResDesc* resd() const { return reinterpret_cast<ResDesc*>(ws + H.resd); }
   ProlongDesc* prold() const { return reinterpret_cast<ProlongDesc*>(ws + H.prold); }
 };
+
+// options.history: the device copy at the end of the workspace
+size_t hist_bytes(const excmg_options* o) {
+  return o->history ? align_up(sizeof(double) * (size_t)o->history_len) : 0;
+}
+
+// The finest level's r.r history -> options.history as ||r_k|| / ||b||, k <= iters.
+excmg_status copy_history(const Ctx& c, const excmg_options* o, const CGState& S) {
+  if (!o->history || !c.hist) return EXCMG_OK;
+  const int n = std::min(S.iter + 1, o->history_len);
+  if (n <= 0) return EXCMG_OK;
+  std::vector<double> h(n);
+  CK(cudaMemcpy(h.data(), c.hist, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < n; ++k) o->history[k] = S.bb > 0 ? sqrt(h[k] / S.bb) : 0.0;
+  return EXCMG_OK;
+}
 
 excmg_status read_states(const Ctx& c, int nprob, std::vector<CGState>& hs) {
   hs.resize(nprob);
@@ -377,6 +395,8 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
       D.w1 = reinterpret_cast<double*>(hd[0].q);
       D.s0 = reinterpret_cast<double*>(hd[0].s0);
       D.s1 = reinterpret_cast<double*>(hd[0].s1);
+      D.hist = hd[0].hist;
+      D.hist_len = hd[0].hist_len;
       double2* pairs = reinterpret_cast<double2*>(c.partials());  // 2 G pairs
       CK(cudaMemsetAsync(c.bar(), 0, 2 * sizeof(unsigned), c.s));  // counter, time-out flag
       if (c.launches) *c.launches += 1;
@@ -865,6 +885,11 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
       CGDesc<double>& d = items.back().d64;
       d.direct = (lev[a] < 2 && o->dsolve == EXCMG_DSOLVE_DIRECT && dsolve_fits(d.g)) ? 1 : 0;
       if (o->fixed_iters) fixed.push_back(o->fixed_iters[lev[a]]);
+      if (c.hist && act[a] == 0 && lev[a] == (int)P[0].lv.size() - 1) {  // options.history
+        Item& it = items.back();
+        it.res.hist = it.d64.hist = c.hist;
+        it.res.hist_len = it.d64.hist_len = o->history_len;
+      }
     }
     excmg_status e = solve_items(c, items, o, state_slots(np), o->fixed_iters ? fixed.data() : nullptr);
     if (e != EXCMG_OK) return e;
@@ -907,10 +932,15 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
       }
   }
   if (c.prof) prof.report(stats, hs);
+  if (c.defer && c.hist) {
+    const excmg_status e = copy_history(c, o, hs[slot_of(0, (int)P[0].lv.size() - 1)]);
+    if (e != EXCMG_OK) return e;
+  }
   return result;
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
 
 // Memory the current device's kernels may read: device or managed memory, or
 // page-locked host memory mapped at the same address (read over the host link).
@@ -977,11 +1007,13 @@ int excmg_num_levels(const excmg_grid* grid) {
 size_t excmg_workspace_size(const excmg_grid* grid, const excmg_options* opt) {
   const auto lv = levels_of(grid);
   if (lv.empty() || !options_ok(opt)) return 0;
-  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt)).bytes;
+  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt)).bytes +
+         hist_bytes(opt);
 }
 
 size_t excmg_workspace_size_batched(int nprob, const excmg_grid* grids, const excmg_options* opt) {
-  if (nprob < 1 || nprob > kMaxProb || !grids || !options_ok(opt) || opt->fixed_iters) return 0;
+  if (nprob < 1 || nprob > kMaxProb || !grids || !options_ok(opt) || opt->fixed_iters || opt->history)
+    return 0;
   size_t total = header_layout(nprob).bytes;
   for (int i = 0; i < nprob; ++i) {
     const auto lv = levels_of(&grids[i]);
@@ -1021,6 +1053,7 @@ excmg_status excmg_solve(const excmg_grid* grid, const double* f, const double* 
   P[0].u = u;
   P[0].base = c.ws + c.H.bytes;
   P[0].L = prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt));
+  if (opt->history) c.hist = reinterpret_cast<double*>(P[0].base + P[0].L.bytes);
   return run_excmg(P, opt, u_tilde, stats, c);
 }
 
@@ -1107,7 +1140,8 @@ excmg_status excmg_grad(const excmg_grid* grid, const double* u, double* ux, dou
 size_t excmg_workspace_size_level(const excmg_grid* grid, const excmg_options* opt) {
   const auto lv = single_level(grid);
   if (lv.empty() || !options_ok(opt)) return 0;
-  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt)).bytes;
+  return header_layout(1).bytes + prob_layout(lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt)).bytes +
+         hist_bytes(opt);
 }
 
 excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_options* opt,
@@ -1132,6 +1166,11 @@ excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_optio
   const int l = (int)lv.size() - 1;
   std::vector<Item> items{make_item(p, l, 0, opt)};
   items[0].eps = opt->eps;
+  if (opt->history) {
+    c.hist = reinterpret_cast<double*>(p.base + p.L.bytes);
+    items[0].res.hist = items[0].d64.hist = c.hist;
+    items[0].res.hist_len = items[0].d64.hist_len = opt->history_len;
+  }
   long long launches = 0;
   Prof prof;
   c.launches = &launches;
@@ -1144,6 +1183,8 @@ excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_optio
   CK(cudaStreamSynchronize(c.s));
   std::vector<CGState> hs;
   e = read_states(c, 1, hs);
+  if (e != EXCMG_OK) return e;
+  e = copy_history(c, opt, hs[0]);
   if (e != EXCMG_OK) return e;
   if (stats) {
     memset(stats, 0, sizeof(*stats));

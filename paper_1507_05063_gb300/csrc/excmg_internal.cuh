@@ -111,6 +111,8 @@ struct CGDesc {
   int blk_begin;          // persistent CG: this problem's blocks are [blk_begin,
   int blk_count;          //   blk_begin + blk_count) of the cooperative grid
   int direct;             // 1: the level is solved by DSOLVE (k_dsolve), not by CG
+  double* hist;           // NULL, or r.r after each CG step k = 1 .. hist_len - 1 (device)
+  int hist_len;
 };
 
 // One problem of a residual phase: r = LHS(u) - RHS(f) (= b - A u_I) in float64,
@@ -133,6 +135,8 @@ struct ResDesc {
   int want_b;           // compute bb (else keep the state's bb)
   int max_iter;
   int fixed;            // exact iteration count
+  double* hist;         // NULL, or receives r.r of the start in hist[0] (device)
+  int hist_len;
 };
 
 // Launch helpers (defined in cg_kernels.cu).  `descs` point to DEVICE copies.
@@ -198,6 +202,8 @@ struct ResidentDesc {
   double* w1;
   double* s0;             // s, even / odd steps
   double* s1;
+  double* hist;           // NULL, or r.r after each CG step k = 1 .. hist_len - 1 (device)
+  int hist_len;
 };
 // Chooses the boxes for grid g; false if the grid does not fit or the device has no
 // cooperative launch.  smem: dynamic shared memory per block.

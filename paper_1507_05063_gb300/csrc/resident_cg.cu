@@ -389,6 +389,7 @@ __global__ void __launch_bounds__(kRsThreads)
         const double2 red = rs_read_pairs(pairs, G, seq);
         const double gn = red.x, dn = red.y;
         iter += 1;
+        if (b == 0 && lane == 0 && D.hist && iter < D.hist_len) D.hist[iter] = gn;
         if (!isfinite(gn) || !isfinite(dn)) {
           status = EXCMG_ERR_NONFINITE;
           stop = 1;

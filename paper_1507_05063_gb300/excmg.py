@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("fixed_iters", ctypes.POINTER(ctypes.c_int)), ("tile_z", ctypes.c_int),
                 ("chunk", ctypes.c_int), ("mixed_min_nodes", ctypes.c_longlong),
                 ("profile", ctypes.c_int), ("dsolve", ctypes.c_int), ("eps_ratio", ctypes.c_double),
-                ("prolong", ctypes.c_int)]
+                ("prolong", ctypes.c_int), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("history_len", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -137,7 +138,7 @@ PROLONG = {"quartic": 0, "quadratic": 1, "linear": 2}
 
 def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
                  inner_tol=1e-4, max_refine=50, fixed_iters=None, tile_z=0, chunk=0, profile=0,
-                 mixed_min_nodes=0, dsolve="direct", eps_ratio=1.0, prolong="quartic"):
+                 mixed_min_nodes=0, dsolve="direct", eps_ratio=1.0, prolong="quartic", history=0):
     o = Options()
     excmg_default_options(ctypes.byref(o))
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else int(precision)
@@ -153,11 +154,21 @@ def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
     o.dsolve = DSOLVE[dsolve] if isinstance(dsolve, str) else int(dsolve)
     o.eps_ratio = float(eps_ratio)
     o.prolong = PROLONG[prolong] if isinstance(prolong, str) else int(prolong)
-    keep = None
+    keep = {}
     if fixed_iters is not None:
-        keep = (ctypes.c_int * len(fixed_iters))(*[int(v) for v in fixed_iters])
-        o.fixed_iters = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+        keep["fixed"] = (ctypes.c_int * len(fixed_iters))(*[int(v) for v in fixed_iters])
+        o.fixed_iters = ctypes.cast(keep["fixed"], ctypes.POINTER(ctypes.c_int))
+    if history:
+        keep["history"] = (ctypes.c_double * int(history))()
+        o.history = ctypes.cast(keep["history"], ctypes.POINTER(ctypes.c_double))
+        o.history_len = int(history)
     return o, keep
+
+
+def _history(keep, iters):
+    """options.history as a list: ||r_k|| / ||b|| for k = 0 .. iters of the finest level."""
+    h = keep.get("history")
+    return None if h is None else list(h[:min(len(h), iters + 1)])
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -221,7 +232,11 @@ def solve(f, g, L, N0, want_utilde=False, stream=None, ws=None, out=None, allow_
                          ctypes.byref(o), _node_array(u, N, "u"), _ptr(ut), _ptr(ws),
                          ws.numel(), ctypes.byref(st), _stream(stream))
     _check(status, "excmg_solve", allow=(2,) if allow_not_converged else ())
-    return {"u": u, "ut": ut, "stats": st.to_dict(), "status": STATUS[status]}
+    sd = st.to_dict()
+    out = {"u": u, "ut": ut, "stats": sd, "status": STATUS[status]}
+    if "history" in _keep:
+        out["history"] = _history(_keep, sd["iters"][-1])
+    return out
 
 
 def grad(u, L, stream=None):
@@ -273,6 +288,8 @@ def cg(f, u, L, stream=None, ws=None, allow_not_converged=False, **opts):
     _check(status, "excmg_cg", allow=(2,) if allow_not_converged else ())
     d = st.to_dict()
     d["status"] = STATUS[status]
+    if "history" in _keep:
+        d["history"] = _history(_keep, d["iters"][0])
     return d
 
 

@@ -305,6 +305,58 @@ def test_pinned_host_inputs_read_in_place(X):
     assert st == 1
 
 
+def _agree_while_large(got, want, floor=1e-8, rel=1e-6):
+    """Residual histories of two implementations agree step by step while the residual
+    is well above the rounding floor (below it the recursive residuals are noise)."""
+    assert len(got) == len(want)
+    for k, (a, b) in enumerate(zip(got, want)):
+        if b > floor:
+            assert a == pytest.approx(b, rel=rel, abs=0), (k, a, b)
+
+
+def test_finest_level_residual_history_matches_oracle(X):
+    """options.history: the finest level's relative residual after each CG step (the
+    persistent engine on 129^3 nodes), step by step equal to the oracle's replay of the
+    same counts; its last entry is the reported relative residual."""
+    N, N0, L = (128, 128, 128), (4, 4, 4), (1.0, 1.0, 1.0)
+    f, g, _ = P.make_inputs(P.PROBLEMS["ex1"], N)
+    res = X.solve(dev(f), dev(g), L, N0, eps=1e-12, history=200, profile=1)
+    st = res["stats"]
+    assert "cg_f64" in st["profile"]
+    h = res["history"]
+    assert len(h) == st["iters"][-1] + 1 and h[-1] == st["relres"][-1] and h[-1] <= 1e-12
+    want = []
+    O.excmg(f, g, L, N, N0, eps=1e-12, dsolve="dense", fixed_iters=st["iters"], history=want,
+            want_utilde=False)
+    _agree_while_large(h, want)
+
+
+@pytest.mark.parametrize("N,engine", [((16, 8, 4), "cg_cluster_f64"), ((64, 32, 16), "cg_resident_f64")])
+def test_cg_residual_history_single_reduction_engines(X, N, engine):
+    """The same history from the single-reduction engines (excmg_cg, fixed step count):
+    their recursive residual follows the standard recurrence's in exact arithmetic."""
+    rng = np.random.default_rng(5)
+    shape = (N[2] + 1, N[1] + 1, N[0] + 1)
+    f = rng.standard_normal(shape)
+    start = rng.standard_normal(shape)
+    L = (1.0, 1.0, 1.0)
+    k = 25
+    u = dev(start)
+    st = X.cg(dev(f), u, L, eps=0.0, fixed_iters=[k], history=k + 1, profile=1)
+    assert engine in st["profile"]
+    want = []
+    O.cg(start, f, O.meshsizes(L, N), 0.0, fixed_iters=k, history=want)
+    assert len(st["history"]) == k + 1
+    _agree_while_large(st["history"], want)
+
+
+def test_history_refused_where_not_supported(X):
+    """MIXED precision has no single CG residual history: the workspace query refuses."""
+    with pytest.raises(X.ExcmgError):
+        f, g, _ = P.make_inputs(P.PROBLEMS["ex1"], (16, 16, 16))
+        X.solve(dev(f), dev(g), (1, 1, 1), (4, 4, 4), precision="mixed", history=10)
+
+
 # --------------------------------------------------------------------------- failure modes
 
 def test_nan_in_f_reports_nonfinite(X):

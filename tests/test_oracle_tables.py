@@ -136,3 +136,21 @@ def test_large_mesh_oracle_takes_table11_step_counts():
             assert int(n) < got <= 2 * int(n)
         else:
             assert got == int(n), (ex, got, n)
+
+
+def test_finest_level_residual_history():
+    """The residual history of the finest level (the figure of Section 5 that plots the
+    relative residual against the CG step): one entry per step plus the start, starting
+    at ||b - A w_h|| / ||b||, ending at the stopping test's value below eps; the start is
+    already small because w_h approximates u_h to fifth order."""
+    N, N0, eps = (32, 32, 32), (4, 4, 4), 1e-12
+    f, g, _ = P.make_inputs(P.PROBLEMS["ex1"], N)
+    hist = []
+    res = O.excmg(f, g, (1, 1, 1), N, N0, eps=eps, dsolve="dense", history=hist)
+    assert len(hist) == res["iters"][-1] + 1
+    assert hist[-1] == res["relres"][-1] and hist[-1] <= eps < hist[-2]
+    w = O.with_boundary(res["w"][-1], g)
+    r0 = O.residual(w, f, res["h"][-1])
+    b = O.rhs_vector(f, g, res["h"][-1])
+    assert hist[0] == pytest.approx(np.sqrt(np.sum(r0 * r0) / np.sum(b * b)), rel=1e-12)
+    assert hist[0] < 1e-6
