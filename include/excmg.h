@@ -159,6 +159,10 @@ typedef struct {
   double prof_ms[EXCMG_KERNEL_KINDS];
   long long prof_launches[EXCMG_KERNEL_KINDS];
   double prof_nodes[EXCMG_KERNEL_KINDS];
+  /* options.profile, single solves: the same launch times summed per level, and over all
+     launches (EXP_true counts to the finest level) */
+  double ms_level[EXCMG_MAX_LEVELS];
+  double ms_total;
 } excmg_stats;
 
 /* Writes the defaults: FP64, eps 1e-9, eps_coarse 1e-12, max_iter 100000,

@@ -278,6 +278,7 @@ struct Prof {
     double nodes;
     bool real;
     int iter_slot;   // >= 0: nodes are per CG step, times the steps of that state slot
+    int level;       // level of the solve the launch worked on (-1: not known)
   };
   std::vector<cudaEvent_t> pool;
   std::vector<Rec> recs;
@@ -306,6 +307,8 @@ struct Prof {
       st->prof_ms[r.kind] += ms;
       st->prof_launches[r.kind] += 1;
       st->prof_nodes[r.kind] += nodes;
+      if (r.level >= 0 && r.level < EXCMG_MAX_LEVELS) st->ms_level[r.level] += ms;
+      st->ms_total += ms;
     }
   }
 };
@@ -315,6 +318,7 @@ struct Ctx {
   Header H;
   cudaStream_t s;
   double* hist = nullptr;         // device r.r history of the finest level (options.history)
+  int level = -1;                 // level being solved (profiling of single solves)
   long long* launches = nullptr;  // kernels launched by this call
   Prof* prof = nullptr;           // set when the call is profiled
   bool persistent_ok = false;     // single-problem CG may use the cooperative kernel
@@ -328,7 +332,7 @@ struct Ctx {
     if (prof->pool[a]) cudaEventRecord(prof->pool[a], s);
     cudaError_t e = fn();
     if (prof->pool[b]) cudaEventRecord(prof->pool[b], s);
-    prof->recs.push_back({kind, a, b, nodes, true, -1});
+    prof->recs.push_back({kind, a, b, nodes, true, -1, level});
     return e;
   }
   CGState* st() const { return reinterpret_cast<CGState*>(ws + H.st); }
@@ -405,7 +409,7 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
         if (c.prof->pool[a]) cudaEventRecord(c.prof->pool[a], c.s);
         CK(launch_cg_resident(D, smem, c.st(), pairs, c.bar(), c.bar_err(), c.s));
         if (c.prof->pool[b]) cudaEventRecord(c.prof->pool[b], c.s);
-        c.prof->recs.push_back({EXCMG_K_CG_RESIDENT_F64, a, b, nodes, true, slots[0]});
+        c.prof->recs.push_back({EXCMG_K_CG_RESIDENT_F64, a, b, nodes, true, slots[0], c.level});
       } else {
         CK(launch_cg_resident(D, smem, c.st(), pairs, c.bar(), c.bar_err(), c.s));
       }
@@ -475,7 +479,7 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
       if (c.prof->pool[a]) cudaEventRecord(c.prof->pool[a], c.s);
       CK(launch());
       if (c.prof->pool[b]) cudaEventRecord(c.prof->pool[b], c.s);
-      c.prof->recs.push_back({kind, a, b, nodes, true, slots[0]});
+      c.prof->recs.push_back({kind, a, b, nodes, true, slots[0], c.level});
     } else {
       CK(launch());
     }
@@ -502,8 +506,8 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
         const size_t e0 = prof->event(), e1 = prof->event(), e2 = prof->event();
         CK(launch_cg_step<T>(n, ddesc, tiles, grid, c.st(), c.partials(), c.counters(), c.s,
                              prof->pool[e0], prof->pool[e1], prof->pool[e2]));
-        prof->recs.push_back({kspmv, e0, e1, nodes, true, -1});
-        prof->recs.push_back({kupd, e1, e2, nodes, true, -1});
+        prof->recs.push_back({kspmv, e0, e1, nodes, true, -1, c.level});
+        prof->recs.push_back({kupd, e1, e2, nodes, true, -1, c.level});
       } else {
         CK(launch_cg_step<T>(n, ddesc, tiles, grid, c.st(), c.partials(), c.counters(), c.s));
       }
@@ -831,6 +835,7 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
   }
   std::vector<ProlongDesc> hp(np);
   for (int phase = 0; phase < maxL; ++phase) {
+    if (np == 1) c.level = phase;
     std::vector<int> act, lev;
     for (int i = 0; i < np; ++i) {
       const int l = phase - (maxL - (int)P[i].lv.size());
@@ -1174,6 +1179,7 @@ excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_optio
   long long launches = 0;
   Prof prof;
   c.launches = &launches;
+  c.level = 0;
   if (opt->profile) c.prof = &prof;
   const long long max_count = opt->fixed_iters ? std::max(opt->max_iter, opt->fixed_iters[0]) : opt->max_iter;
   c.persistent_ok = (long long)kMaxGrid * (2 * max_count + 4) < (1LL << 32);

@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("relres", ctypes.c_double * MAX_LEVELS), ("launches", ctypes.c_longlong),
                 ("prof_ms", ctypes.c_double * KERNEL_KINDS),
                 ("prof_launches", ctypes.c_longlong * KERNEL_KINDS),
-                ("prof_nodes", ctypes.c_double * KERNEL_KINDS)]
+                ("prof_nodes", ctypes.c_double * KERNEL_KINDS),
+                ("ms_level", ctypes.c_double * MAX_LEVELS), ("ms_total", ctypes.c_double)]
 
     def to_dict(self):
         n = self.levels
@@ -68,7 +69,8 @@ class Stats(ctypes.Structure):
                 "profile": {KERNEL_NAMES[k]: {"ms": float(self.prof_ms[k]),
                                               "launches": int(self.prof_launches[k]),
                                               "nodes": float(self.prof_nodes[k])}
-                            for k in range(KERNEL_KINDS) if self.prof_launches[k] > 0}}
+                            for k in range(KERNEL_KINDS) if self.prof_launches[k] > 0},
+                "ms_level": list(self.ms_level[:n]), "ms_total": float(self.ms_total)}
 
 
 _P = ctypes.c_void_p
