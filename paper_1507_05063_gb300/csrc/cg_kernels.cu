@@ -768,6 +768,17 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
     TR* __restrict__ rout = reinterpret_cast<TR*>(d.r);
     const TileXYZ c = res_tile_coords(g, d.t, t - d.tile_begin);
     const int i = c.x0 + tx, jb = c.y0 + R * ty;  // rows jb .. jb + R - 1
+    if (c.x0 >= g.nx || c.y0 >= g.ny || c.z0 >= g.nz) {
+      // a tile of boundary nodes only (the last column, row or plane of the grid and the
+      // padding beyond it): r = 0, no arithmetic
+      for (int kc = c.z0; kc < c.z1; ++kc)
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const int j = jb + q;
+          if (i <= g.nx && j <= g.ny) rout[i + j * g.sy + (long long)kc * g.sz] = (TR)0.0;
+        }
+      continue;
+    }
     const bool colx = (i > 0) && (i < g.nx);
     const bool want_b = d.want_b != 0;
     const bool use_f = d.src == nullptr;
