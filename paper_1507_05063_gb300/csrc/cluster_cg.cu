@@ -81,36 +81,33 @@ __device__ __forceinline__ double xor_sum(double v, int from) {
 }
 
 // Sums of (a, b) over every thread of the cluster, returned in every lane of warp 0
-// (bit-identical in every CTA); other warps get 0.  Contains one cluster barrier.
+// (bit-identical in every CTA); other warps get 0.  Contains one cluster barrier.  Both
+// sums share each float64 warp instruction: lanes 0-15 carry a, lanes 16-31 carry b (on
+// GB300 a float64 warp instruction costs the narrow FP64 pipe the same for one sum or
+// two, and a step waits on this chain).
 template <int NW>
 __device__ double2 cluster_sum2(double a, double b, double* s_park, double* slots,
                                 unsigned me, int csize) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // the CTA's sums: values parked in shared memory, added by warp 0 (NW per lane, then a
-  // butterfly) -- few float64 warp instructions, which share the narrow FP64 pipe
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, h = lane & 15;
+  // the CTA's sums: values parked in shared memory, added by warp 0 (2 NW per lane as a
+  // pairwise tree, then a butterfly over 16 lanes)
   s_park[threadIdx.x] = a;
   s_park[32 * NW + threadIdx.x] = b;
   __syncthreads();
   if (warp == 0) {
-    double va[NW], vb[NW];
+    const double* src = s_park + (lane < 16 ? 0 : 32 * NW);
+    double v[2 * NW];
 #pragma unroll
-    for (int u = 0; u < NW; ++u) {
-      va[u] = s_park[lane + 32 * u];
-      vb[u] = s_park[32 * NW + lane + 32 * u];
-    }
+    for (int u = 0; u < 2 * NW; ++u) v[u] = src[h + 16 * u];
 #pragma unroll
-    for (int w = 1; w < NW; w *= 2)  // pairwise: a dependence chain of log2(NW) adds
+    for (int w = 1; w < 2 * NW; w *= 2)
 #pragma unroll
-      for (int u = 0; u + w < NW; u += 2 * w) {
-        va[u] += va[u + w];
-        vb[u] += vb[u + w];
-      }
-    double ta = va[0], tb = vb[0];
-    // a full butterfly: every lane holds the CTA's sums (lane c stores into CTA c, and
-    // the cluster may have more CTAs than this CTA has warps -- a CTA given a wrong
-    // partial would take other decisions than its peers)
-    ta = xor_sum(ta, 16);
-    tb = xor_sum(tb, 16);
+      for (int u = 0; u + w < 2 * NW; u += 2 * w) v[u] += v[u + w];
+    const double r = xor_sum(v[0], 8);
+    // every lane holds both CTA sums (lane c stores into CTA c, and the cluster may have
+    // more CTAs than this CTA has warps -- a CTA given a wrong partial would take other
+    // decisions than its peers)
+    const double ta = __shfl_sync(0xffffffffu, r, 0), tb = __shfl_sync(0xffffffffu, r, 16);
     if (lane < csize) {
       st_cl(slots + me, (unsigned)lane, ta);
       st_cl(slots + kClMax + me, (unsigned)lane, tb);
@@ -123,16 +120,15 @@ __device__ double2 cluster_sum2(double a, double b, double* s_park, double* slot
   }
   double2 t = make_double2(0.0, 0.0);
   if (warp == 0) {
-    double ta = lane < csize ? slots[lane] : 0.0;
-    double tb = lane < csize ? slots[kClMax + lane] : 0.0;
-    // a butterfly over the smallest power of two >= csize lanes: fixed order (csize is
-    // the same in every CTA), so identical in every CTA
+    // the C slots of a in lanes 0-15, of b in lanes 16-31; a butterfly over the smallest
+    // power of two >= csize lanes of each half: fixed order (csize is the same in every
+    // CTA), so identical in every CTA
+    double v = h < csize ? slots[(lane < 16 ? 0 : kClMax) + h] : 0.0;
     int from = 1;
     while (from < csize) from <<= 1;
-    ta = xor_sum(ta, from >> 1);
-    tb = xor_sum(tb, from >> 1);
-    t.x = __shfl_sync(0xffffffffu, ta, 0);
-    t.y = __shfl_sync(0xffffffffu, tb, 0);
+    v = xor_sum(v, from >> 1);
+    t.x = __shfl_sync(0xffffffffu, v, 0);
+    t.y = __shfl_sync(0xffffffffu, v, 16);
   }
   return t;
 }
