@@ -47,6 +47,29 @@ Tiling make_tiling(const Grid3& g, int tz) {
   return t;
 }
 
+// Slab depth of the residual kernel: among 1..64 the one minimising (rounds of the tiles
+// that hold interior nodes over the residual grid) x (planes per tile, halo included).
+// Tiles of boundary nodes only cost nothing (k_residual writes zeros there), and every
+// block of a round waits for the slowest, so a deep slab that leaves blocks idle loses
+// to a thin one that fills every block.
+int choose_res_tz(const Grid3& g, int grid_blocks, int requested) {
+  if (requested > 0) return requested;
+  int best = 16;
+  double best_cost = 1e300;
+  const int cands[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64};
+  for (int tz : cands) {
+    const long long tiles = (long long)((g.nx + kTX - 1) / kTX) *
+                            ((g.ny + kTY * kResRows - 1) / (kTY * kResRows)) * ((g.nz + tz - 1) / tz);
+    const long long rounds = (tiles + grid_blocks - 1) / grid_blocks;
+    const double cost = (double)rounds * (std::min(tz, g.nz + 1) + 2);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = tz;
+    }
+  }
+  return best;
+}
+
 Tiling make_res_tiling(const Grid3& g, int tz) {
   Tiling t = make_tiling(g, tz);
   t.nty = (g.ny + 1 + kTY * kResRows - 1) / (kTY * kResRows);
@@ -546,13 +569,13 @@ struct Item {
   double relres;
 };
 
-ResDesc make_res(const Grid3& g, const Tiling& t, int slot, const double* x, View f,
+ResDesc make_res(const Grid3& g, int tile_z, int slot, const double* x, View f,
                  const double* src) {
   ResDesc r;
   memset(&r, 0, sizeof(r));
   r.g = g;
   r.A = make_coef(g);
-  r.t = make_res_tiling(g, t.tz);
+  r.t = make_res_tiling(g, choose_res_tz(g, residual_grid(1LL << 40), tile_z));
   r.slot = slot;
   r.u = x;
   r.f = f;
@@ -760,7 +783,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   const double ratio = o->eps_ratio > 0 ? o->eps_ratio : 1.0;
   it.eps = (l < 2) ? o->eps_coarse : o->eps * std::pow(ratio, (double)((int)p.lv.size() - 1 - l));
   it.nodes = g.nodes();
-  it.res = make_res(g, t, slot, p.level_u(l), p.fview(l), nullptr);
+  it.res = make_res(g, o->tile_z, slot, p.level_u(l), p.fview(l), nullptr);
   CGDesc<double>& d = it.d64;
   d.g = g;
   d.A = it.res.A;
@@ -1221,8 +1244,7 @@ excmg_status excmg_residual(const excmg_grid* grid, const double* f, const doubl
   c.H = header_layout(1);
   c.s = static_cast<cudaStream_t>(stream);
   const Grid3 g = make_grid(grid->Nx, grid->Ny, grid->Nz, grid->Lx, grid->Ly, grid->Lz);
-  const Tiling t = make_tiling(g, choose_tz(g, persistent_grid(1LL << 40), 0));
-  ResDesc d = make_res(g, t, 0, u, View{f, 1, g.sy, g.sz}, nullptr);
+  ResDesc d = make_res(g, 0, 0, u, View{f, 1, g.sy, g.sz}, nullptr);
   d.r = r;
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
   CK(cudaMemcpyAsync(c.resd(), &d, sizeof(d), cudaMemcpyHostToDevice, c.s));

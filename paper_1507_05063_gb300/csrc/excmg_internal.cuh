@@ -86,8 +86,10 @@ struct Tiling {
   __host__ __device__ long long count() const { return (long long)ntx * nty * ntz; }
 };
 Tiling make_tiling(const Grid3& g, int tz);
-// The residual kernel's tiling: kTY * kResRows rows per tile, the same x-width and tz.
+// The residual kernel's tiling: kTY * kResRows rows per tile, the same x-width, slab
+// depth tz (choose_res_tz: the residual's own model of its launch).
 Tiling make_res_tiling(const Grid3& g, int tz);
+int choose_res_tz(const Grid3& g, int grid_blocks, int requested);
 int choose_tz(const Grid3& g, int grid_blocks, int requested);
 
 // One problem of a CG phase.

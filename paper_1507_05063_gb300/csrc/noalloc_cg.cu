@@ -119,7 +119,7 @@ extern "C" excmg_status excmg_cg_noalloc(const excmg_grid* grid, const double* f
   memset(&rd, 0, sizeof(rd));
   rd.g = g;
   rd.A = make_coef(g);
-  rd.t = make_res_tiling(g, t.tz);
+  rd.t = make_res_tiling(g, choose_res_tz(g, residual_grid(1LL << 40), opt->tile_z));
   rd.slot = 0;
   rd.u = u;
   rd.f = View{f, 1, g.sy, g.sz};
