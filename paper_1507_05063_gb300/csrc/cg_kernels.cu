@@ -49,10 +49,40 @@ __device__ double block_sum(double v) {
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x < 32) {
-    for (int k = lane; k < (int)blockDim.x; k += 32) t += s_v[k];
-    t = warp_sum(t);
+    // kThreads / 32 values per lane as a pairwise tree (a short dependence chain)
+    double w[kThreads / 32];
+#pragma unroll
+    for (int u = 0; u < kThreads / 32; ++u) w[u] = s_v[lane + 32 * u];
+#pragma unroll
+    for (int d = 1; d < kThreads / 32; d *= 2)
+#pragma unroll
+      for (int u = 0; u + d < kThreads / 32; u += 2 * d) w[u] += w[u + d];
+    t = warp_sum(w[0]);
   }
   return t;
+}
+
+// Warp-0 sum of src[0 .. n) from global memory (through L2) in a fixed order: each lane
+// takes the values lane, lane + 32, ... in chunks of kSumChunk loads in flight, sums a
+// chunk as a pairwise tree, then the lanes reduce by shuffles.  Valid in lane 0.
+constexpr int kSumChunk = 8;
+__device__ __forceinline__ double warp0_sum_global(const double* src, int n) {
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  for (int i0 = 0; i0 < n; i0 += 32 * kSumChunk) {
+    double w[kSumChunk];
+#pragma unroll
+    for (int u = 0; u < kSumChunk; ++u) {
+      const int i = i0 + lane + 32 * u;
+      w[u] = i < n ? __ldcg(src + i) : 0.0;
+    }
+#pragma unroll
+    for (int d = 1; d < kSumChunk; d *= 2)
+#pragma unroll
+      for (int u = 0; u + d < kSumChunk; u += 2 * d) w[u] += w[u + d];
+    acc += w[0];
+  }
+  return warp_sum(acc);
 }
 
 template <typename D>
@@ -103,15 +133,8 @@ __device__ void publish_and_finish(int nprob, const int* s_active, const double*
     __threadfence();
     double sums[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double acc = 0.0;
-      const volatile double* src = partials + ((long long)p * NV + v) * G;
-      if (threadIdx.x < 32) {
-        for (int i = threadIdx.x; i < G; i += 32) acc += src[i];
-        acc = warp_sum(acc);
-      }
-      sums[v] = acc;
-    }
+    for (int v = 0; v < NV; ++v)
+      sums[v] = threadIdx.x < 32 ? warp0_sum_global(partials + ((long long)p * NV + v) * G, G) : 0.0;
     if (threadIdx.x == 0) {
       fin(p, sums);
       counters[p] = 0u;
@@ -531,12 +554,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* err) {
 // Sum of n partials in a fixed order, identical in every block (warp 0 only: the adds
 // are float64).  Result in thread 0.
 __device__ double sum_partials_all(const double* part, int n) {
-  double acc = 0.0;
-  if (threadIdx.x < 32) {
-    for (int i = threadIdx.x; i < n; i += 32) acc += __ldcg(part + i);
-    acc = warp_sum(acc);
-  }
-  return acc;
+  return threadIdx.x < 32 ? warp0_sum_global(part, n) : 0.0;
 }
 
 #ifndef EXCMG_PERSIST_MIN_BLOCKS
