@@ -10,12 +10,14 @@
 //     A^{-1} b = (2/nx)(2/ny)(2/nz) S Lambda^{-1} S b,
 //     Lambda(kx,ky,kz) = c0 + fx mu_x + fy mu_y + fz mu_z + exy mu_x mu_y + exz mu_x mu_z
 //                        + eyz mu_y mu_z.
-// The level's b is the residual of its zero-interior start (computed by the residual
-// kernel: r = b - A 0 = b, lift included), so one block per problem transforms b along x,
-// y and z (dense sine matrices in shared memory: (mx + my + mz) FMA per unknown per
-// direction of the transform), divides, transforms back, writes u's interior, and
-// checks the result: r = b - A u on the interior, r.r into the problem's CG state (0
-// steps, done).
+// One block per problem forms b from f and the Dirichlet data (the residual of the start
+// with g on the boundary and zero inside: -RHS(f) minus the lift), writes g into the
+// level's boundary nodes, transforms b along x, y and z (dense sine matrices in shared
+// memory, built from a table of the 2 n_d distinct values sin(pi m / n_d): (mx + my + mz)
+// FMA per unknown per direction of the transform), divides, transforms back, writes u's
+// interior, and checks the result: r = b - A u on the interior, r.r and b.b into the
+// problem's CG state (0 steps, done).  The cascade launches no boundary initialisation
+// and no residual for these levels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -74,21 +76,60 @@ __global__ void __launch_bounds__(kDsThreads)
   double* Sx = W + n;        // mx * mx
   double* Sy = Sx + mx * mx; // my * my
   double* Sz = Sy + my * my; // mz * mz
-  // sine matrices: sin(pi i k / n_d) with the argument reduced exactly to [0, 2)
-  auto fill = [&](double* M, int m, int nd) {
+  double* C = Sz + mz * mz;  // mx + my + mz: 2 cos(pi k / n_d), the eigenvalues of T
+  double* T = C + mx + my + mz;  // 2 (nx + ny + nz): sin(pi m / n_d), m = 0 .. 2 n_d - 1
+  double* Tx = T;
+  double* Ty = Tx + 2 * g.nx;
+  double* Tz = Ty + 2 * g.ny;
+  for (int t = threadIdx.x; t < 2 * g.nx; t += kDsThreads) Tx[t] = sinpi((double)t / g.nx);
+  for (int t = threadIdx.x; t < 2 * g.ny; t += kDsThreads) Ty[t] = sinpi((double)t / g.ny);
+  for (int t = threadIdx.x; t < 2 * g.nz; t += kDsThreads) Tz[t] = sinpi((double)t / g.nz);
+  for (int t = threadIdx.x; t < mx + my + mz; t += kDsThreads) {
+    const int ax = t < mx ? 0 : (t < mx + my ? 1 : 2);
+    const int k = t - (ax == 0 ? 0 : (ax == 1 ? mx : mx + my)) + 1;
+    C[t] = 2.0 * cospi((double)k / (ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz)));
+  }
+  // g on the level's boundary nodes
+  const long long nodes = g.nodes();
+  for (long long o = threadIdx.x; o < nodes; o += kDsThreads) {
+    const int i = (int)(o % g.sy), j = (int)((o / g.sy) % (g.ny + 1)), k = (int)(o / g.sz);
+    if (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz) d.x[o] = d.gb.at(i, j, k);
+  }
+  __syncthreads();
+  // sine matrices: sin(pi i k / n_d) = table[(i k) mod 2 n_d]
+  auto fill = [&](double* M, const double* tab, int m, int nd) {
     for (int t = threadIdx.x; t < m * m; t += kDsThreads) {
       const int k = t / m + 1, i = t % m + 1;
-      M[t] = sinpi((double)((i * k) % (2 * nd)) / nd);
+      M[t] = tab[(i * k) % (2 * nd)];
     }
   };
-  fill(Sx, mx, g.nx);
-  fill(Sy, my, g.ny);
-  fill(Sz, mz, g.nz);
-  // b on the interior (the residual of the zero-interior start)
+  fill(Sx, Tx, mx, g.nx);
+  fill(Sy, Ty, my, g.ny);
+  fill(Sz, Tz, mz, g.nz);
+  // b on the interior: -(A-stencil of the start: g on the boundary, 0 inside) - RHS(f)
+  const Coef A = d.A;
+  auto ub = [&](int i, int j, int k) -> double {
+    return (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz) ? d.gb.at(i, j, k) : 0.0;
+  };
+  double acc_b = 0.0;
   for (int t = threadIdx.x; t < n; t += kDsThreads) {
-    const int ix = t % mx, iy = (t / mx) % my, iz = t / (mx * my);
-    V[t] = d.r[(ix + 1) + (iy + 1) * g.sy + (long long)(iz + 1) * g.sz];
+    const int i = t % mx + 1, j = (t / mx) % my + 1, k = t / (mx * my) + 1;
+    const View& F = d.f;
+    const double rhs2 = fma(6.0, F.at(i, j, k), ((F.at(i - 1, j, k) + F.at(i + 1, j, k)) +
+                                                 (F.at(i, j - 1, k) + F.at(i, j + 1, k)) +
+                                                 (F.at(i, j, k - 1) + F.at(i, j, k + 1))));
+    const double SX = ub(i - 1, j, k) + ub(i + 1, j, k), SY = ub(i, j - 1, k) + ub(i, j + 1, k);
+    const double SZ = ub(i, j, k - 1) + ub(i, j, k + 1);
+    const double EXY = (ub(i - 1, j - 1, k) + ub(i + 1, j - 1, k)) + (ub(i - 1, j + 1, k) + ub(i + 1, j + 1, k));
+    const double EXZ = (ub(i - 1, j, k - 1) + ub(i + 1, j, k - 1)) + (ub(i - 1, j, k + 1) + ub(i + 1, j, k + 1));
+    const double EYZ = (ub(i, j - 1, k - 1) + ub(i, j + 1, k - 1)) + (ub(i, j - 1, k + 1) + ub(i, j + 1, k + 1));
+    const double lift = fma(A.fx, SX, fma(A.fy, SY, fma(A.fz, SZ, fma(A.exy, EXY, fma(A.exz, EXZ, A.eyz * EYZ)))));
+    const double b = fma(-0.5, rhs2, -lift);
+    V[t] = b;
+    d.r[i + j * g.sy + (long long)k * g.sz] = b;
+    acc_b = fma(b, b, acc_b);
   }
+  const double bb = ds_block_sum(acc_b, s_park);
   __syncthreads();
   ds_axis(V, W, Sx, mx, my, mz, 0);
   __syncthreads();
@@ -96,13 +137,13 @@ __global__ void __launch_bounds__(kDsThreads)
   __syncthreads();
   ds_axis(V, W, Sz, mx, my, mz, 2);
   __syncthreads();
-  const Coef A = d.A;
+  const double* Cx = C;
+  const double* Cy = C + mx;
+  const double* Cz = C + mx + my;
   const double scale = 8.0 / ((double)g.nx * g.ny * g.nz);
   for (int t = threadIdx.x; t < n; t += kDsThreads) {
     const int ix = t % mx, iy = (t / mx) % my, iz = t / (mx * my);
-    const double ux = 2.0 * cospi((double)(ix + 1) / g.nx);
-    const double uy = 2.0 * cospi((double)(iy + 1) / g.ny);
-    const double uz = 2.0 * cospi((double)(iz + 1) / g.nz);
+    const double ux = Cx[ix], uy = Cy[iy], uz = Cz[iz];
     const double lam = A.c0 + A.fx * ux + A.fy * uy + A.fz * uz + A.exy * ux * uy + A.exz * ux * uz +
                        A.eyz * uy * uz;
     W[t] = W[t] * (scale / lam);
@@ -141,10 +182,16 @@ __global__ void __launch_bounds__(kDsThreads)
   const double rr = ds_block_sum(acc, s_park);
   if (threadIdx.x == 0) {
     S->rr = rr;
+    S->rr0 = rr;
+    S->bb = bb;
+    S->alpha = S->beta = S->pq = 0.0;
+    S->tol2 = 0.0;
     S->iter = 0;
+    S->max_iter = 0;
+    S->fixed = 0;
     S->first = 0;
     S->done = 1;
-    S->status = isfinite(rr) ? EXCMG_OK : EXCMG_ERR_NONFINITE;
+    S->status = isfinite(rr) && isfinite(bb) ? EXCMG_OK : EXCMG_ERR_NONFINITE;
   }
 }
 
@@ -152,7 +199,8 @@ __global__ void __launch_bounds__(kDsThreads)
 
 size_t dsolve_smem(const Grid3& g) {
   const size_t mx = g.nx - 1, my = g.ny - 1, mz = g.nz - 1;
-  return sizeof(double) * (2 * mx * my * mz + mx * mx + my * my + mz * mz);
+  return sizeof(double) *
+         (2 * mx * my * mz + mx * mx + my * my + mz * mz + (mx + my + mz) + 2 * (g.nx + g.ny + g.nz));
 }
 
 static int g_ds_max_smem = 0;

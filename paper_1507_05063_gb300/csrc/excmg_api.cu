@@ -627,7 +627,7 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     it.relres = 0.0;
     ResDesc r = it.res;
     r.tile_begin = rtiles;
-    rtiles += r.t.count();
+    if (!it.d64.direct) rtiles += r.t.count();  // DSOLVE levels form their own b
     it.d64.tile_begin = tiles;
     it.d32.tile_begin = tiles;
     tiles += it.d64.t.count();
@@ -648,7 +648,7 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
       r.max_iter = fixed ? fixed[a] : o->max_iter;
     }
     it.res = r;
-    hr.push_back(r);
+    if (!it.d64.direct) hr.push_back(r);
   }
   if (n == 0) return EXCMG_OK;
   double nodes_sum = 0.0;
@@ -661,12 +661,18 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
       slots.push_back(it.d64.slot);
     }
     const int grid = tiles_grid(tiles);
-    CK(cudaMemcpyAsync(c.resd(), hr.data(), sizeof(ResDesc) * n, cudaMemcpyHostToDevice, c.s));
+    const int nres = (int)hr.size();
+    double res_nodes = 0.0;
+    for (auto& it : items)
+      if (!it.d64.direct) res_nodes += (double)it.nodes;
     CK(cudaMemcpyAsync(c.cgd(), hd.data(), sizeof(CGDesc<double>) * n, cudaMemcpyHostToDevice, c.s));
-    CK(c.timed(EXCMG_K_RESIDUAL, nodes_sum, [&] {
-      return launch_residual(false, n, c.resd(), rtiles, residual_grid(rtiles), c.st(), c.partials(),
-                             c.counters(), c.s);
-    }));
+    if (nres > 0) {
+      CK(cudaMemcpyAsync(c.resd(), hr.data(), sizeof(ResDesc) * nres, cudaMemcpyHostToDevice, c.s));
+      CK(c.timed(EXCMG_K_RESIDUAL, res_nodes, [&] {
+        return launch_residual(false, nres, c.resd(), rtiles, residual_grid(rtiles), c.st(), c.partials(),
+                               c.counters(), c.s);
+      }));
+    }
     // DSOLVE levels: one direct solve each (their states are done with 0 steps, so the
     // CG engines skip them)
     int ndirect = 0;
@@ -877,7 +883,9 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
       const int l = lev[a];
       const Grid3 g = p.grid(l);
       if (l < 2) {
-        CK(c.timed(EXCMG_K_INIT, (double)g.nodes(), [&] { return launch_boundary_init(g, p.gview(l), p.level_u(l), c.s); }));
+        // DSOLVE by the direct solve writes the boundary itself (and forms b)
+        if (!(o->dsolve == EXCMG_DSOLVE_DIRECT && dsolve_fits(g)))
+          CK(c.timed(EXCMG_K_INIT, (double)g.nodes(), [&] { return launch_boundary_init(g, p.gview(l), p.level_u(l), c.s); }));
       } else {
         ProlongDesc d;
         d.g = g;
@@ -912,6 +920,10 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
       // DSOLVE (levels 0 and 1 of the cascade): the direct solve when the grid fits
       CGDesc<double>& d = items.back().d64;
       d.direct = (lev[a] < 2 && o->dsolve == EXCMG_DSOLVE_DIRECT && dsolve_fits(d.g)) ? 1 : 0;
+      if (d.direct) {
+        d.f = P[act[a]].fview(lev[a]);
+        d.gb = P[act[a]].gview(lev[a]);
+      }
       if (o->fixed_iters) fixed.push_back(o->fixed_iters[lev[a]]);
       if (c.hist && act[a] == 0 && lev[a] == (int)P[0].lv.size() - 1) {  // options.history
         Item& it = items.back();

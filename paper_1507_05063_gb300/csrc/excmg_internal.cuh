@@ -113,6 +113,8 @@ struct CGDesc {
   int blk_begin;          // persistent CG: this problem's blocks are [blk_begin,
   int blk_count;          //   blk_begin + blk_count) of the cooperative grid
   int direct;             // 1: the level is solved by DSOLVE (k_dsolve), not by CG
+  View f;                 // DSOLVE: f and the Dirichlet data at this level's nodes
+  View gb;
   double* hist;           // NULL, or r.r after each CG step k = 1 .. hist_len - 1 (device)
   int hist_len;
 };
