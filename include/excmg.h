@@ -127,7 +127,7 @@ typedef struct {
 
 /* DSOLVE of Algorithm 1 (levels 0 and 1).  DIRECT: the exact discrete solution by the
    three-dimensional discrete sine transform, which diagonalises the 19-point operator on
-   the box (grids whose interior fits one block's shared memory, about 13,000 unknowns;
+   the box (grids whose interior fits one block's shared memory, about 9,000 unknowns;
    larger coarse grids fall back to CG); stats.iters = 0 for these levels and relres the
    residual of the direct solution.  CG: CG from zero to eps_coarse. */
 typedef enum { EXCMG_DSOLVE_DIRECT = 0, EXCMG_DSOLVE_CG = 1 } excmg_dsolve;
@@ -160,7 +160,8 @@ typedef struct {
   long long prof_launches[EXCMG_KERNEL_KINDS];
   double prof_nodes[EXCMG_KERNEL_KINDS];
   /* options.profile, single solves: the same launch times summed per level, and over all
-     launches (EXP_true counts to the finest level) */
+     launches (EXP_true counts to the finest level; the direct DSOLVE of levels 0 and 1 is
+     one launch, counted to level 0) */
   double ms_level[EXCMG_MAX_LEVELS];
   double ms_total;
 } excmg_stats;

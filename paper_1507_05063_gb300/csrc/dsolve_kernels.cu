@@ -16,7 +16,8 @@
 // memory, built from a table of the 2 n_d distinct values sin(pi m / n_d): (mx + my + mz)
 // FMA per unknown per direction of the transform), divides, transforms back, writes u's
 // interior, and checks the result: r = b - A u on the interior, r.r and b.b into the
-// problem's CG state (0 steps, done).  The cascade launches no boundary initialisation
+// problem's CG state (0 steps, done).  Everything but u's nodes and the state stays in
+// shared memory, so one launch can solve levels 0 and 1 side by side.  The cascade launches no boundary initialisation
 // and no residual for these levels.
 #include <cuda_runtime.h>
 
@@ -73,7 +74,9 @@ __global__ void __launch_bounds__(kDsThreads)
   const int n = mx * my * mz;
   double* V = s_ds;          // n
   double* W = V + n;         // n
-  double* Sx = W + n;        // mx * mx
+  double* Bv = W + n;        // n: b (kept for the check; the workspace vectors are shared
+                             // by the levels this launch solves together)
+  double* Sx = Bv + n;       // mx * mx
   double* Sy = Sx + mx * mx; // my * my
   double* Sz = Sy + my * my; // mz * mz
   double* C = Sz + mz * mz;  // mx + my + mz: 2 cos(pi k / n_d), the eigenvalues of T
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kDsThreads)
     const double lift = fma(A.fx, SX, fma(A.fy, SY, fma(A.fz, SZ, fma(A.exy, EXY, fma(A.exz, EXZ, A.eyz * EYZ)))));
     const double b = fma(-0.5, rhs2, -lift);
     V[t] = b;
-    d.r[i + j * g.sy + (long long)k * g.sz] = b;
+    Bv[t] = b;
     acc_b = fma(b, b, acc_b);
   }
   const double bb = ds_block_sum(acc_b, s_park);
@@ -174,8 +177,7 @@ __global__ void __launch_bounds__(kDsThreads)
     const double Au = fma(A.c0, V[t], fma(A.fx, SX, fma(A.fy, SY, fma(A.fz, SZ,
                       fma(A.exy, EXY, fma(A.exz, EXZ, A.eyz * EYZ))))));
     const long long o = (ix + 1) + (iy + 1) * g.sy + (long long)(iz + 1) * g.sz;
-    const double r = d.r[o] - Au;
-    d.r[o] = r;
+    const double r = Bv[t] - Au;
     d.x[o] = V[t];
     acc = fma(r, r, acc);
   }
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(kDsThreads)
 size_t dsolve_smem(const Grid3& g) {
   const size_t mx = g.nx - 1, my = g.ny - 1, mz = g.nz - 1;
   return sizeof(double) *
-         (2 * mx * my * mz + mx * mx + my * my + mz * mz + (mx + my + mz) + 2 * (g.nx + g.ny + g.nz));
+         (3 * mx * my * mz + mx * mx + my * my + mz * mz + (mx + my + mz) + 2 * (g.nx + g.ny + g.nz));
 }
 
 static int g_ds_max_smem = 0;

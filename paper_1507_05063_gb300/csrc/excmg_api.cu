@@ -863,16 +863,28 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
     }
   }
   std::vector<ProlongDesc> hp(np);
+  // Levels 0 and 1 are independent (each DSOLVE starts from the Dirichlet data alone): when
+  // both take the direct solve, a problem's level 1 joins the phase of its level 0, and
+  // one k_dsolve launch serves both.
+  auto direct_level = [&](const Prob& p, int l) {
+    return l < 2 && l < (int)p.lv.size() && o->dsolve == EXCMG_DSOLVE_DIRECT && dsolve_fits(p.grid(l));
+  };
+  std::vector<char> level1_early(np, 0);
   for (int phase = 0; phase < maxL; ++phase) {
     if (np == 1) c.level = phase;
     std::vector<int> act, lev;
     for (int i = 0; i < np; ++i) {
       const int l = phase - (maxL - (int)P[i].lv.size());
-      if (l >= 0) {
+      if (l < 0 || (l == 1 && level1_early[i])) continue;
+      act.push_back(i);
+      lev.push_back(l);
+      if (l == 0 && direct_level(P[i], 0) && direct_level(P[i], 1)) {
         act.push_back(i);
-        lev.push_back(l);
+        lev.push_back(1);
+        level1_early[i] = 1;
       }
     }
+    if (act.empty()) continue;
     const int na = (int)act.size();
     // 1. initial guess: zero inside (levels 0, 1) or w_h = EXP_finite(u_2h, u_4h)
     int npro = 0;
@@ -884,7 +896,7 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
       const Grid3 g = p.grid(l);
       if (l < 2) {
         // DSOLVE by the direct solve writes the boundary itself (and forms b)
-        if (!(o->dsolve == EXCMG_DSOLVE_DIRECT && dsolve_fits(g)))
+        if (!direct_level(p, l))
           CK(c.timed(EXCMG_K_INIT, (double)g.nodes(), [&] { return launch_boundary_init(g, p.gview(l), p.level_u(l), c.s); }));
       } else {
         ProlongDesc d;
