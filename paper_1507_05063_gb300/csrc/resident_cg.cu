@@ -194,6 +194,10 @@ __global__ void __launch_bounds__(kRsThreads)
     w.valid = gi < g.nx && gj < g.ny && gk < g.nz;
     return w;
   };
+  // boxes of at most one node per thread: this thread's node, computed once (the index
+  // arithmetic divides by the box extents) instead of in every step
+  const Own mine = own_node(threadIdx.x < B ? threadIdx.x : 0);
+  auto node_of = [&](int q) -> Own { return shallow ? mine : own_node(q); };
   // shell position h (0 .. ext - B - 1): the 2 z-faces, then the 2 y-faces, then the 2
   // x-faces of the extended box
   const int zf = EX * EY, yf = EX * BZ, xf = BY * BZ;
@@ -266,24 +270,31 @@ __global__ void __launch_bounds__(kRsThreads)
   // the scalar arithmetic (zero on the boundary)
   double hr[kRsHB], hw[kRsHB], hs[kRsHB];
   int he[kRsHB];
+  // this thread's shell nodes (index in R, offset in the level's arrays or -1 outside the
+  // interior), computed once: after each wait the loads issue at once
+  int ho[kRsHB];
+#pragma unroll
+  for (int u = 0; u < kRsHB; ++u) {
+    const int h = threadIdx.x + u * kRsThreads;
+    he[u] = -1;
+    ho[u] = -1;
+    if (h < nshell) {
+      int gi, gj, gk;
+      shell_node(h, he[u], gi, gj, gk);
+      if (interior(gi, gj, gk)) ho[u] = gi + gj * g.sy + gk * g.sz;
+    }
+  }
   auto load_halo = [&](int par) {
     const double* Rg = par ? D.r1 : D.r;
     const double* Wg = par ? D.w1 : D.w0;
     const double* Sg = par ? D.s1 : D.s0;
 #pragma unroll
     for (int u = 0; u < kRsHB; ++u) {
-      const int h = threadIdx.x + u * kRsThreads;
-      he[u] = -1;
       hr[u] = hw[u] = hs[u] = 0.0;
-      if (h < nshell) {
-        int gi, gj, gk;
-        shell_node(h, he[u], gi, gj, gk);
-        if (interior(gi, gj, gk)) {
-          const long long o = gi + gj * g.sy + (long long)gk * g.sz;
-          hr[u] = __ldcg(Rg + o);
-          hw[u] = __ldcg(Wg + o);
-          hs[u] = __ldcg(Sg + o);
-        }
+      if (ho[u] >= 0) {
+        hr[u] = __ldcg(Rg + ho[u]);
+        hw[u] = __ldcg(Wg + ho[u]);
+        hs[u] = __ldcg(Sg + ho[u]);
       }
     }
   };
@@ -328,7 +339,7 @@ __global__ void __launch_bounds__(kRsThreads)
     double* Sn = par ? D.s0 : D.s1;
     // 1. own nodes: p, s, x, r; publish r and s
     for (int q = threadIdx.x; q < B; q += kRsThreads) {
-      const Own n = own_node(q);
+      const Own n = node_of(q);
       if (!n.valid) continue;
       const int e = n.e;
       const long long o = n.o;
@@ -363,7 +374,7 @@ __global__ void __launch_bounds__(kRsThreads)
     double acc_g = 0.0;
     acc_d = 0.0;
     for (int q = threadIdx.x; q < B; q += kRsThreads) {
-      const Own n = own_node(q);
+      const Own n = node_of(q);
       double w = 0.0;
       if (n.valid) {
         const double r = R[n.e];
