@@ -90,7 +90,7 @@ typedef struct {
   int precision;           /* excmg_precision */
   double eps;              /* relative-residual tolerance on levels >= 2: CG stops when
                               ||A u - b||_2 <= eps ||b||_2, b the assembled right-hand
-                              side with its Dirichlet lift (Algorithm 1, line 7) */
+                              side with its Dirichlet lift (the stopping test of Algorithm 1) */
   double eps_coarse;       /* same test on levels 0 and 1 when DSOLVE is CG */
   int max_iter;            /* cap on CG iterations per level (per inner solve) */
   double inner_tol;        /* MIXED: inner float32 CG stops at ||r|| <= inner_tol ||r0|| */
@@ -105,15 +105,15 @@ typedef struct {
   int profile;             /* nonzero: time every kernel launch of excmg_solve / excmg_cg
                               with CUDA events on the caller's stream (stats.prof_*);
                               single-problem calls only; adds two event records per launch */
-  int dsolve;              /* excmg_dsolve: how levels 0 and 1 are solved (Algorithm 1,
-                              lines 1-2) */
+  int dsolve;              /* excmg_dsolve: how levels 0 and 1 are solved (DSOLVE of
+                              Algorithm 1) */
   double eps_ratio;        /* per-level tolerance: level l >= 2 of L levels stops at
                               eps * eps_ratio^(L-1-l), so the finest level uses eps and each
                               coarser one eps_ratio times more (64 = 2^6 follows the
                               sixth-order error of u~ from level to level); 1 (the default)
                               or 0: the uniform eps of Algorithm 1 */
   int prolong;             /* excmg_prolong: how the initial guess w_h of levels >= 2 is
-                              formed (Algorithm 1, line 6); default QUARTIC */
+                              formed (the initial guess of Algorithm 1); default QUARTIC */
   double* history;         /* HOST array or NULL: the residual history of the finest
                               level (the relative residual against the CG step, as in the
                               figure of Section 5 that plots it): history[k] =
@@ -132,7 +132,7 @@ typedef struct {
    residual of the direct solution.  CG: CG from zero to eps_coarse. */
 typedef enum { EXCMG_DSOLVE_DIRECT = 0, EXCMG_DSOLVE_CG = 1 } excmg_dsolve;
 
-/* Initial guess of levels >= 2 (Algorithm 1, line 6).  QUARTIC: EXP_finite(u_2h, u_4h) --
+/* Initial guess of levels >= 2 (Algorithm 1, before the CG loop).  QUARTIC: EXP_finite(u_2h, u_4h) --
    extrapolation to the grid-2h nodes (eqs. jiedian, zhongdian), then tri-quartic
    interpolation over cells of 2x2x2 grid-4h elements (eq. inter); the method of the paper.
    The other two exist to measure what EXP_finite saves: QUADRATIC keeps the extrapolation
@@ -186,7 +186,7 @@ size_t excmg_workspace_size(const excmg_grid* grid, const excmg_options* opt);
  * nodes of grid 2h, tri-quartic Lagrange interpolation eq. inter on every cell of 2x2x2
  * elements of grid 4h), then CG from w_h (interior) until the relative residual is at
  * most eps.  On the finest level, optionally u~_h = EXP_true(u_h, u_2h) (eqs. t1,
- * chenlin; line 10).
+ * chenlin; the optional last step).
  *   f        [in]  finest-grid node array: the Poisson right-hand side on ALL nodes
  *                  (the compact RHS uses f at face neighbours, which may be boundary
  *                  nodes).
@@ -258,7 +258,7 @@ excmg_status excmg_adjoint(const excmg_grid* grid, const double* dLdu,
 /* ---- single steps of the path, exported for parity tests and custom drivers ---- */
 
 /*
- * excmg_exp_finite -- EXP_finite(u_2h, u_4h) of Algorithm 1 line 6 / Section 3.3 onto
+ * excmg_exp_finite -- EXP_finite(u_2h, u_4h) of Algorithm 1 / Section 3.3 onto
  * grid h = `grid`'s finest level: u2h and u4h are node arrays of the grids with
  * Nx/2 and Nx/4 cells.  Writes w (node array of grid h) on all nodes; if g is not NULL
  * the boundary nodes of w are set to g (the CG start), otherwise they keep their
@@ -268,7 +268,7 @@ excmg_status excmg_exp_finite(const excmg_grid* grid, const double* u2h, const d
                               const double* g, double* w, void* stream);
 
 /*
- * excmg_exp_true -- EXP_true(u_h, u_2h) of Algorithm 1 line 10 (Section 3.3): eq. (t1)
+ * excmg_exp_true -- EXP_true(u_h, u_2h) of Algorithm 1, its optional last step (Section 3.3): eq. (t1)
  * (16 u_h - u_2h)/15 at the nodes of grid 2h, eq. (chenlin) u_h + (d_a + d_b)/30 along
  * every edge, face diagonal or space diagonal through the other nodes (averaged over the
  * diagonals), d = u_h - u_2h.  uh: grid h node array; u2h: Nx/2 grid.  Needs Nx, Ny, Nz
@@ -282,7 +282,7 @@ excmg_status excmg_exp_true(const excmg_grid* grid, const double* uh, const doub
 size_t excmg_workspace_size_level(const excmg_grid* grid, const excmg_options* opt);
 
 /*
- * excmg_cg -- CG on the grid Nx x Ny x Nz alone (Algorithm 1 lines 7-9; Nx0.. ignored):
+ * excmg_cg -- CG on the grid Nx x Ny x Nz alone (the CG loop of Algorithm 1; Nx0.. ignored):
  * from the interior values of u (boundary entries of u must already hold g) until
  * ||r|| <= opt->eps ||b|| (or exactly opt->fixed_iters[0] iterations; MIXED refines with
  * float32 inner solves).  u [in/out].  Workspace: excmg_workspace_size_level().

@@ -9,7 +9,7 @@ Array convention: a node array on a grid of Nx x Ny x Nz cells has numpy shape
 (Nz+1, Ny+1, Nx+1) and is indexed [k, j, i]; node (i, j, k) sits at (i hx, j hy, k hz)
 (Section 2).  "Interior" arrays have shape (Nz-1, Ny-1, Nx-1).
 
-Readings of the paper taken here (each is also listed in the design doc):
+Readings of the paper taken here (the CUDA path takes the same ones):
 * Sign (Section 2, eq. FD): the printed left-hand side is negative definite; the SPD
   matrix is A = -(printed LHS restricted to the interior), b = -(printed RHS minus the
   boundary terms).  ``residual`` returns b - A u_I = LHS(u) - RHS(f).
@@ -142,11 +142,11 @@ def rhs_vector(f, g, h):
 
 
 # --------------------------------------------------------------------------------------
-# Algorithm 1, lines 7-9: CG with the relative-residual stopping criterion
+# Algorithm 1, its WHILE loop: CG with the relative-residual stopping criterion
 # --------------------------------------------------------------------------------------
 
 def cg(u0, f, h, eps, max_iter=100000, fixed_iters=None, history=None):
-    """Unpreconditioned CG on A u_I = b from the initial guess u0 (Algorithm 1 l.7-9).
+    """Unpreconditioned CG on A u_I = b from the initial guess u0 (the WHILE loop of Algorithm 1).
 
     One CG step per pass of the WHILE loop; the loop test ||r||_2 <= eps ||b||_2 is
     made before every step on CG's recursively updated residual r.  ``fixed_iters``
@@ -200,7 +200,7 @@ def dense_matrix(n_cells, h):
 
 
 def dense_solve(g, f, h):
-    """DSOLVE of Algorithm 1 l.1-2 as a dense Cholesky solve (tiny grids only)."""
+    """DSOLVE of Algorithm 1 (the two coarsest grids) as a dense Cholesky solve (tiny grids only)."""
     nz, ny, nx = f.shape
     M = dense_matrix((nx - 1, ny - 1, nz - 1), h)
     b = rhs_vector(f, g, h).ravel()
@@ -346,7 +346,7 @@ def extrapolate_true(uh, u2h):
 
 
 def exp_finite(u2h, u4h):
-    """EXP_finite(u_2h, u_4h) of Algorithm 1 l.6 (Section 3.3), on all nodes of grid h.
+    """EXP_finite(u_2h, u_4h) of Algorithm 1, the initial guess (Section 3.3), on all nodes of grid h.
 
     1. w^2 at the 125 known nodes of every interpolation cell (the nodes of grid 2h) by
        ``extrapolate_fd``;
@@ -436,7 +436,7 @@ def prolong_linear(u2h):
 
 
 def prolong(kind, u2h, u4h):
-    """w_h of Algorithm 1, line 6, by the named prolongation ('quartic' = EXP_finite)."""
+    """w_h of Algorithm 1 (the initial guess) by the named prolongation ('quartic' = EXP_finite)."""
     if kind == "quartic":
         return exp_finite(u2h, u4h)
     if kind == "quadratic":

@@ -1,5 +1,5 @@
 // Matrix-free stencil CG for the 19-point compact scheme (Section 2, eq. compact) and
-// the CG loop of Algorithm 1 (lines 7-9).
+// the CG loop of Algorithm 1 (one step per pass of its WHILE loop).
 //
 // One CG step is two launches, both persistent over z-slab tiles of kTX x kTY columns:
 //   k_dir_spmv_dot : p_new = r + beta p_old (p = r on the first step), q = A p_new,

@@ -1,6 +1,6 @@
 // Level-to-level transfers of Algorithm 1 (Section 3.3):
-//   EXP_finite(u_2h, u_4h) -> w_h   (line 6; eqs. jiedian, zhongdian, inter)
-//   EXP_true(u_h, u_2h)    -> u~_h  (line 10; eqs. t1, chenlin)
+//   EXP_finite(u_2h, u_4h) -> w_h   (the initial guess; eqs. jiedian, zhongdian, inter)
+//   EXP_true(u_h, u_2h)    -> u~_h  (the optional last step; eqs. t1, chenlin)
 // and the adjoint's transposed right-hand-side / lift operators.
 //
 // EXP_finite works on bricks of 32 x 8 x 8 fine cells (four interpolation cells along x,
