@@ -204,6 +204,33 @@ def oracle_solve_seconds(wl, f, g):
     return time.perf_counter() - t0, res
 
 
+class Replicas:
+    """The N ranks of a run: each solves its own copy of the workload (independent
+    problems, no collective on the data path); they meet only at the barriers around the
+    timed region and in the max of their times.  `dist` is torch.distributed (or None for
+    one rank); the max travels in a float64 tensor on `device`."""
+
+    def __init__(self, world, device, dist=None):
+        self.world, self.device, self.dist = world, device, dist
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, v):
+        if self.world == 1:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def rate(self, units_per_rank, steps, ms):
+        """Whole-job throughput: the units all ranks processed over the slowest rank's time
+        (ms, already the max over ranks)."""
+        return units_per_rank * self.world * steps / (ms / 1e3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -274,16 +301,9 @@ def main():
     ws = X.workspace(X.solve_workspace_bytes(L, N, N0, **opts), device)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Replicas(world, device, dist if world > 1 else None)
+    barrier = ranks.barrier
+    max_over_ranks = ranks.max
 
     for _ in range(max(args.warmup, 0)):
         X.solve(fd, gd, L, N0, ws=ws, out=ud, **opts)
@@ -307,7 +327,7 @@ def main():
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms)
     stats = res["stats"]
-    value = n_unk * world * args.steps / (ms / 1e3)
+    value = ranks.rate(n_unk, args.steps, ms)
 
     # ---- accuracy of the timed solution (host evaluation)
     uh = ud.cpu().numpy()
@@ -440,7 +460,7 @@ def main():
                                            "stream while the next step solves"}}
     best = min(e2e_modes, key=lambda k: e2e_modes[k]["ms_per_step"])
     ms_e2e = e2e_modes[best]["ms_per_step"] * args.steps
-    e2e_value = n_unk * world * args.steps / (ms_e2e / 1e3)
+    e2e_value = ranks.rate(n_unk, args.steps, ms_e2e)
     h2d = e2e_modes[best]["h2d_bytes_per_step"]
     d2h = f.nbytes
 
