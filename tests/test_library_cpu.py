@@ -57,7 +57,8 @@ def test_invalid_grids_rejected(X, N, N0):
 def test_invalid_options_rejected(X):
     g = X.make_grid((1, 1, 1), (32, 32, 32), (4, 4, 4))
     for kw in ({"precision": 7}, {"eps": -1.0}, {"max_iter": -3}, {"precision": "mixed", "inner_tol": 2.0},
-               {"mixed_min_nodes": -1}):
+               {"mixed_min_nodes": -1}, {"eps_ratio": -1.0}, {"eps_ratio": float("nan")},
+               {"prolong": 7}, {"dsolve": 5}, {"precision": "mixed", "history": 8}):
         o, _ = X.make_options(**kw)
         assert X.excmg_workspace_size(ctypes.byref(g), ctypes.byref(o)) == 0
 
@@ -82,3 +83,18 @@ def test_bench_tables_cover_every_kernel_kind():
     for k in excmg.KERNEL_NAMES:
         assert k in bench.ALGO and k in bench.KERNEL_SYMBOL and k in bench.KERNEL_SOURCE, k
         assert os.path.exists(os.path.join(ROOT, "paper_1507_05063_gb300", "csrc", bench.KERNEL_SOURCE[k]))
+
+
+def test_history_option_sizes_the_workspace(X):
+    """options.history adds its device copy to the workspace (history_len doubles, aligned);
+    a history pointer with no length, and batched solves, are refused."""
+    g = X.make_grid((1, 1, 1), (32, 32, 32), (4, 4, 4))
+    o0, _ = X.make_options()
+    o1, _k1 = X.make_options(history=100)
+    base = X.excmg_workspace_size(ctypes.byref(g), ctypes.byref(o0))
+    assert X.excmg_workspace_size(ctypes.byref(g), ctypes.byref(o1)) >= base + 800
+    o1.history_len = 0
+    assert X.excmg_workspace_size(ctypes.byref(g), ctypes.byref(o1)) == 0
+    o2, _k2 = X.make_options(history=10)
+    grids = (X.Grid * 2)(g, g)
+    assert X.excmg_workspace_size_batched(2, grids, ctypes.byref(o2)) == 0
