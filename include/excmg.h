@@ -166,9 +166,10 @@ typedef struct {
   double ms_total;
 } excmg_stats;
 
-/* Writes the defaults: FP64, eps 1e-9, eps_coarse 1e-12, max_iter 100000,
+/* Writes the defaults: precision FP64, eps 1e-9, eps_coarse 1e-12, max_iter 100000,
    inner_tol 1e-4, max_refine 50, fixed_iters NULL, tile_z 0, chunk 0,
-   mixed_min_nodes 0, profile 0. */
+   mixed_min_nodes 0, profile 0, dsolve DIRECT, eps_ratio 1 (uniform tolerance),
+   prolong QUARTIC, history NULL, history_len 0. */
 void excmg_default_options(excmg_options* opt);
 
 /* Human-readable name of a status code (static string). */

@@ -98,3 +98,22 @@ def test_history_option_sizes_the_workspace(X):
     o2, _k2 = X.make_options(history=10)
     grids = (X.Grid * 2)(g, g)
     assert X.excmg_workspace_size_batched(2, grids, ctypes.byref(o2)) == 0
+
+
+def test_default_options_match_the_header(X):
+    """excmg_default_options writes the values its declaration lists, every field set."""
+    o = X.Options()
+    ctypes.memset(ctypes.byref(o), 0x5A, ctypes.sizeof(o))  # no field may keep this
+    X.excmg_default_options(ctypes.byref(o))
+    want = {"precision": 0, "eps": 1e-9, "eps_coarse": 1e-12, "max_iter": 100000,
+            "inner_tol": 1e-4, "max_refine": 50, "tile_z": 0, "chunk": 0,
+            "mixed_min_nodes": 0, "profile": 0, "dsolve": 0, "eps_ratio": 1.0,
+            "prolong": 0, "history_len": 0}
+    for name, v in want.items():
+        assert getattr(o, name) == v, name
+    assert not o.fixed_iters and not o.history
+    header = open(os.path.join(ROOT, "include", "excmg.h")).read()
+    doc = re.search(r"/\* Writes the defaults:(.*?)\*/", header, re.S).group(1)
+    fields = [n for n, _ in X.Options._fields_]
+    for name in fields:
+        assert name in doc, "header's default list omits " + name
