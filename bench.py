@@ -19,7 +19,7 @@ import os
 
 # the CPU oracle baseline is timed single-threaded
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
+    os.environ[_v] = "1"
 
 import argparse  # noqa: E402
 import hashlib  # noqa: E402
@@ -195,6 +195,29 @@ def interior_unknowns(N):
     return (N[0] - 1) * (N[1] - 1) * (N[2] - 1)
 
 
+def host_cpu():
+    """The host's CPU model and logical core count, for the CPU baseline's record."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key, _, val = line.partition(":")
+                if key.strip().lower() == "model name":
+                    model = val.strip()
+                    break
+    except OSError:
+        pass
+    if model is None:  # Arm hosts list no model name in /proc/cpuinfo
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            model = next((ln.split(":", 1)[1].strip() for ln in out.splitlines()
+                          if ln.lower().startswith("model name")), None)
+        except (OSError, subprocess.SubprocessError):
+            pass
+    import platform
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
 def oracle_solve_seconds(wl, f, g):
     """One complete oracle EXCMG solve of the workload; returns (seconds, u)."""
     import oracle as O
@@ -252,7 +275,7 @@ def run_reference(args):
             "config": {"workload": DESCRIPTION[args.workload], "unknowns": n},
             "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
                              "sample": "each step: one complete oracle EXCMG solve of the workload "
-                                       "(numpy, float64, single thread)"},
+                                       "(numpy, float64, single thread)", "host": host_cpu()},
             "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -528,6 +551,7 @@ def main():
                                 "sample": "one complete oracle EXCMG solve of the same workload "
                                           "(numpy float64, single thread)",
                                 "seconds": secs, "iters_per_level": ores["iters"],
+                                "host": host_cpu(),
                                 "gpu_vs_oracle_rel_linf": float(np.max(np.abs(uh - uo)) / np.max(np.abs(uo)))}
     if rank == 0:
         print(json.dumps(line), flush=True)
