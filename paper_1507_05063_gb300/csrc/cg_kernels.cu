@@ -739,6 +739,17 @@ __device__ double perim_lift(const double* __restrict__ u, const Grid3& g, const
   return (LC + lt(k - 1)) + lt(k + 1);
 }
 
+// Twice the right-hand side of eq. (compact) at interior node (i, j, k): 6 f_c + the 6
+// face values of f (the face values are re-read through L1 by the neighbouring threads),
+// or -2 b when b is given directly.  o is the node's offset.
+__device__ __forceinline__ double res_rhs2(const ResDesc& d, int i, int j, int k, long long o) {
+  if (d.src != nullptr) return -2.0 * d.src[o];
+  const View& F = d.f;
+  return fma(6.0, F.at(i, j, k), ((F.at(i - 1, j, k) + F.at(i + 1, j, k)) +
+                                  (F.at(i, j - 1, k) + F.at(i, j + 1, k)) +
+                                  (F.at(i, j, k - 1) + F.at(i, j, k + 1))));
+}
+
 // Each thread marches its kResRows rows of one x-column through the tile's planes.  Per
 // plane it loads the (kResRows + 2) x 3 neighbourhood (through the read-only cache:
 // neighbouring threads share the lines; no staging, no block barrier) and forms, per row,
@@ -748,12 +759,16 @@ __device__ double perim_lift(const double* __restrict__ u, const Grid3& g, const
 // the same grouping as (SW + SE) + (NW + NE)); the sum at plane k is C_k + T_{k-1} +
 // T_{k+1}.  The first and last plane of a tile contribute T only.  b (for ||b||) is
 // -RHS away from the boundary; next to a z-boundary plane its lift is that plane's T;
-// next to an x or y boundary face it is formed by perim_lift.
+// next to a y boundary face it is formed by perim_lift (the whole warp is such a row).
+// Next to an x boundary face only one lane of the warp is such a node: those nodes are
+// left out of the plane loop and formed after it, one lane per plane, so a warp issues
+// the lift once for up to 32 planes instead of once per plane for one lane.
 template <typename TR>
 __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
     k_residual(int nprob, const ResDesc* __restrict__ descs, long long total_tiles,
                CGState* st, double* partials, unsigned* counters) {
   constexpr int R = kResRows;
+  static_assert(kTX == 32, "one warp per x-run of a residual tile row");
   __shared__ int s_active[kMaxProb];
   __shared__ double s_part[2 * kMaxProb];
   for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
@@ -799,7 +814,6 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
     }
     const bool colx = (i > 0) && (i < g.nx);
     const bool want_b = d.want_b != 0;
-    const bool use_f = d.src == nullptr;
     const Coef A = d.A;
     double Cm1[R], Tm1[R], Tm2[R];
 #pragma unroll
@@ -833,29 +847,23 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
           const long long o = i + j * g.sy + (long long)kc * g.sz;
           double rv = 0.0;
           if (colx && j > 0 && j < g.ny && kc > 0 && kc < g.nz) {
-            // twice the right-hand side of eq. (compact), 6 f_c + the 6 face values of f
-            // (the face values are re-read through L1 by the neighbouring threads); the
-            // factor 1/2 is applied inside the fused multiply-adds below, exactly
-            const View& F = d.f;
-            const double rhs2 =
-                use_f ? fma(6.0, F.at(i, j, kc), ((F.at(i - 1, j, kc) + F.at(i + 1, j, kc)) +
-                                                  (F.at(i, j - 1, kc) + F.at(i, j + 1, kc)) +
-                                                  (F.at(i, j, kc - 1) + F.at(i, j, kc + 1))))
-                      : -2.0 * d.src[o];
+            // twice the right-hand side; the factor 1/2 is applied inside the fused
+            // multiply-adds below, exactly
+            const double rhs2 = res_rhs2(d, i, j, kc, o);
             if (d.rhs_out) d.rhs_out[o] = -0.5 * rhs2;
             // LHS(u) - RHS = -(A-stencil of u over all 19 nodes) - RHS
             rv = fma(-0.5, rhs2, -((Cm1[q] + Tm2[q]) + Tk));
             acc_r = fma(rv, rv, acc_r);
             if (want_b) {
-              const bool perim = (i == 1 || i == g.nx - 1 || j == 1 || j == g.ny - 1);
-              if (!perim && kc >= 2 && kc <= g.nz - 2) {
+              const bool yface = (j == 1 || j == g.ny - 1), xface = (i == 1 || i == g.nx - 1);
+              if (!yface && !xface && kc >= 2 && kc <= g.nz - 2) {
                 acc_b4 = fma(rhs2, rhs2, acc_b4);  // b = -RHS here
-              } else {
-                const double lift = perim ? perim_lift(u, g, A, i, j, kc)
+              } else if (yface || !xface) {
+                const double lift = yface ? perim_lift(u, g, A, i, j, kc)
                                           : (kc == 1 ? Tm2[q] : 0.0) + (kc == g.nz - 1 ? Tk : 0.0);
                 const double bv = fma(-0.5, rhs2, -lift);
                 acc_b = fma(bv, bv, acc_b);
-              }
+              }  // else next to an x face only: after the plane loop
             }
           }
           rout[o] = (TR)rv;
@@ -863,6 +871,31 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
         Tm2[q] = Tm1[q];
         Tm1[q] = Tk;
         Cm1[q] = Ck;
+      }
+    }
+    if (want_b) {
+      // b of the tile's nodes next to an x face and no y face (columns 1 and nx - 1, rows
+      // 2 .. ny - 2): the warp of such a row takes them one lane per plane.  A warp is one
+      // x-run of 32 columns (kTX = 32), so its columns are c.x0 .. c.x0 + 31 in every row.
+      const int lane = threadIdx.x & 31;
+      const int k_lo = max(c.z0, 1), k_hi = min(c.z1, g.nz);  // interior planes of the tile
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int j = jb + q;
+        if (j < 2 || j > g.ny - 2) continue;
+        for (int side = 0; side < 2; ++side) {
+          const int xi = side == 0 ? 1 : g.nx - 1;
+          if (side == 1 && xi == 1) break;  // nx = 2: a single interior column
+          if (xi < c.x0 || xi >= c.x0 + kTX) continue;
+          for (int k0 = k_lo; k0 < k_hi; k0 += 32) {
+            const int kc = k0 + lane;
+            if (kc < k_hi) {
+              const long long o = xi + j * g.sy + (long long)kc * g.sz;
+              const double bv = fma(-0.5, res_rhs2(d, xi, j, kc, o), -perim_lift(u, g, A, xi, j, kc));
+              acc_b = fma(bv, bv, acc_b);
+            }
+          }
+        }
       }
     }
   }

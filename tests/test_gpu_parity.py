@@ -60,6 +60,27 @@ def test_residual_kernel(X, N, L):
     assert bn == pytest.approx(np.linalg.norm(O.rhs_vector(f, u, h)), rel=1e-12)
 
 
+@pytest.mark.parametrize("N,tz", [((36, 10, 70), 0), ((36, 10, 70), 1), ((36, 10, 70), 5),
+                                  ((36, 10, 70), 64), ((2, 6, 40), 64), ((30, 5, 9), 3),
+                                  ((64, 64, 33), 40)])
+def test_residual_norms_every_slab_depth(X, N, tz):
+    """||r|| / ||b|| of a level's residual launch (b with its Dirichlet lift) at any slab
+    depth: the lift at nodes next to an x face is formed after each tile's plane loop, one
+    lane per plane in passes of 32 planes, so slabs deeper than 32, both x faces in one
+    warp (nx <= 32) and a single interior column (nx = 2) all reach every such node once.
+    history[0] of a zero-step CG is that ratio."""
+    L = (1.0, 0.7, 2.0)
+    rng = np.random.default_rng(9)
+    shape = (N[2] + 1, N[1] + 1, N[0] + 1)
+    f = rng.standard_normal(shape)
+    start = rng.standard_normal(shape)
+    h = O.meshsizes(L, N)
+    want = np.linalg.norm(O.residual(start, f, h)) / np.linalg.norm(O.rhs_vector(f, start, h))
+    st = X.cg(dev(f), dev(start), L, eps=0.0, fixed_iters=[0], history=1, tile_z=tz)
+    assert st["iters"] == [0]
+    assert st["history"][0] == pytest.approx(want, rel=1e-12, abs=0)
+
+
 @pytest.mark.parametrize("N,L", [((32, 16, 24), (1.0, 1.0, 1.0)), ((64, 8, 8), (2.0, 1.0, 0.5)),
                                  ((8, 8, 8), (1, 1, 1))])
 def test_exp_finite_kernel(X, N, L):
