@@ -42,7 +42,8 @@ typedef enum {
   EXCMG_ERR_NOT_CONVERGED = 2, /* a CG loop hit max_iter before its tolerance */
   EXCMG_ERR_CUDA = 3,          /* a CUDA call failed */
   EXCMG_ERR_NONFINITE = 4,     /* NaN/Inf met in a CG reduction (e.g. NaN in f or g) */
-  EXCMG_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait ran out */
+  EXCMG_ERR_TIMEOUT = 5,       /* a bounded device wait (a grid barrier of a cooperative
+                                  CG launch) ran out; the kernel returned instead */
   EXCMG_ERR_WORKSPACE = 6      /* workspace NULL, too small or misaligned */
 } excmg_status;
 
@@ -89,8 +90,8 @@ typedef struct {
 typedef struct {
   int precision;           /* excmg_precision */
   double eps;              /* relative-residual tolerance on levels >= 2: CG stops when
-                              ||A u - b||_2 <= eps ||b||_2, b the assembled right-hand
-                              side with its Dirichlet lift (the stopping test of Algorithm 1) */
+                              ||A u - b||_2 <= eps ||f_h||_2 (the WHILE test of Algorithm 1),
+                              ||f_h|| as options.rhs_norm reads it */
   double eps_coarse;       /* same test on levels 0 and 1 when DSOLVE is CG */
   int max_iter;            /* cap on CG iterations per level (per inner solve) */
   double inner_tol;        /* MIXED: inner float32 CG stops at ||r|| <= inner_tol ||r0|| */
@@ -123,7 +124,30 @@ typedef struct {
                               unchanged.  excmg_solve and excmg_cg (its one level), FP64
                               only; the workspace grows by history_len doubles */
   int history_len;         /* entries of `history` (>= 1 when history is set) */
+  int rhs_norm;            /* excmg_rhs_norm: the reading of ||f_h|| in the stopping test */
+  double wait_timeout_ms;  /* bound on every device-side wait of a cooperative CG launch
+                              (its grid barriers and tensor-copy completions): a wait that
+                              runs out ends the launch with EXCMG_ERR_TIMEOUT; 0 = 20000 */
+  int test_phantom_blocks; /* TEST ONLY, 0 otherwise: adds this many members that are never
+                              launched to the block team of each cooperative CG launch of
+                              levels above 2^19 nodes, so that its first grid barrier cannot
+                              complete and its wait must run out (with a short
+                              wait_timeout_ms, to check that the call returns
+                              EXCMG_ERR_TIMEOUT and the context stays usable) */
 } excmg_options;
+
+/* ||f_h||_2 in the WHILE test ||A_h u_h - f_h|| > eps ||f_h|| of Algorithm 1.  The paper
+   defines f_h (Section 2, after eq. FD) as the right-hand side vector of eq. (compact),
+   but its printed tables fit two different readings:
+   LIFT (default): the 2-norm of the assembled right-hand side b of eq. (FD), Dirichlet
+     lift included -- this reproduces the finest-grid CG step counts of Table 11;
+   FORCING: the 2-norm of (6 f + the six face values of f)/2 over the interior nodes, the
+     right-hand side of eq. (compact) alone -- this reproduces the errors of Tables 1-10
+     on the 128^3 meshes, where the algebraic error shows, and takes more CG steps.
+     Where that vector is zero (f = 0, e.g. Example 2) FORCING uses LIFT: no relative
+     test against a zero norm can pass.
+   stats.relres and options.history are relative to the same norm. */
+typedef enum { EXCMG_RHS_NORM_LIFT = 0, EXCMG_RHS_NORM_FORCING = 1 } excmg_rhs_norm;
 
 /* DSOLVE of Algorithm 1 (levels 0 and 1).  DIRECT: the exact discrete solution by the
    three-dimensional discrete sine transform, which diagonalises the 19-point operator on
@@ -150,8 +174,9 @@ typedef struct {
   int N[EXCMG_MAX_LEVELS][3];        /* cells per level */
   int iters[EXCMG_MAX_LEVELS];       /* CG iterations per level (summed over refinements) */
   int refinements[EXCMG_MAX_LEVELS]; /* MIXED: refinement steps per level */
-  double relres[EXCMG_MAX_LEVELS];   /* final ||r||/||b|| per level (recursive residual
-                                        for FP64; true float64 residual for MIXED) */
+  double relres[EXCMG_MAX_LEVELS];   /* final ||r||/||f_h|| per level (recursive residual
+                                        for FP64; true float64 residual for MIXED; ||f_h||
+                                        as options.rhs_norm reads it) */
   long long launches;                /* kernels this call launched (all levels) */
   /* options.profile: per kernel kind (excmg_kernel_kind), summed CUDA-event time of its
      launches that did work, their count, and the node count they covered in total
@@ -169,7 +194,8 @@ typedef struct {
 /* Writes the defaults: precision FP64, eps 1e-9, eps_coarse 1e-12, max_iter 100000,
    inner_tol 1e-4, max_refine 50, fixed_iters NULL, tile_z 0, chunk 0,
    mixed_min_nodes 0, profile 0, dsolve DIRECT, eps_ratio 1 (uniform tolerance),
-   prolong QUARTIC, history NULL, history_len 0. */
+   prolong QUARTIC, history NULL, history_len 0, rhs_norm LIFT, wait_timeout_ms 0
+   (20 s), test_phantom_blocks 0. */
 void excmg_default_options(excmg_options* opt);
 
 /* Human-readable name of a status code (static string). */
@@ -306,8 +332,11 @@ excmg_status excmg_residual(const excmg_grid* grid, const double* f, const doubl
 /* ---- an entry point for callers that cannot allocate device memory ----
  *
  * excmg_cg_noalloc -- the same computation as excmg_cg (float64 CG on the grid
- * Nx x Ny x Nz from the interior of u, with the same options, outputs and status codes),
- * but it takes no workspace: its scratch is a device array built into the library.
+ * Nx x Ny x Nz from the interior of u, with the same outputs and status codes), but it
+ * takes no workspace: its scratch is a device array built into the library.  Options
+ * are checked as for excmg_cg; precision must be EXCMG_FP64, and options.history and
+ * options.profile must be unset (EXCMG_ERR_INVALID_ARG otherwise: they need host-side
+ * buffers and events that this entry point does not keep).
  * The paper has no counterpart; this exists for callers that must not allocate device
  * memory -- an application or framework that owns all device memory through its own
  * pool, code that cannot afford cudaMalloc's implicit synchronisation, or a binding

@@ -196,7 +196,8 @@ struct FinRes {
     const ResDesc& d = descs[p];
     CGState& S = st[d.slot];
     const double rr = s[0];
-    const double bb = d.want_b ? s[1] : S.bb;
+    // s[1] = ||b||^2 (lift included), s[2] = ||RHS(f)||^2: the two readings of ||f_h||
+    const double bb = !d.want_b ? S.bb : (d.forcing && s[2] > 0.0) ? s[2] : s[1];
     S.rr = rr;
     S.rr0 = rr;
     S.bb = bb;
@@ -211,6 +212,8 @@ struct FinRes {
     S.tol2 = d.fixed ? -1.0 : fmax(d.tol_b2 * bb, d.tol_r2 * rr);
     if (d.hist && d.hist_len > 0) d.hist[0] = rr;
     S.done = d.fixed ? (d.max_iter <= 0) : (rr <= S.tol2 || d.max_iter <= 0);
+    // no step allowed and the start does not pass the test: the level is unconverged
+    if (!d.fixed && d.max_iter <= 0 && !(rr <= S.tol2)) S.status = EXCMG_ERR_NOT_CONVERGED;
     if (!isfinite(rr) || !isfinite(bb)) {
       S.status = EXCMG_ERR_NONFINITE;
       S.done = 1;
@@ -282,7 +285,9 @@ __device__ __forceinline__ T spmv_tile(const CGDesc<T>& d, long long lt, bool fi
   T* __restrict__ q = d.q;
   const TileXYZ c = tile_coords(g, d.t, lt);
   const int i = c.x0 + tx, j = c.y0 + ty;
-  const bool own = (i <= g.nx) && (j <= g.ny);
+  // own nodes include the padding columns nx + 1 .. sy - 1 of a padded float32 array,
+  // which get p = q = 0 (the flat update then leaves them zero)
+  const bool own = (i < g.sy) && (j <= g.ny);
   const bool inxy = (i > 0) && (i < g.nx) && (j > 0) && (j < g.ny);
   const T c0 = (T)d.A.c0, fx = (T)d.A.fx, fy = (T)d.A.fy, fz = (T)d.A.fz;
   const T exy = (T)d.A.exy, exz = (T)d.A.exz, eyz = (T)d.A.eyz;
@@ -331,7 +336,7 @@ __device__ __forceinline__ T spmv_tile(const CGDesc<T>& d, long long lt, bool fi
 // share of r.r.
 template <typename T>
 __device__ __forceinline__ T update_tile(const CGDesc<T>& d, long long lt, T alpha,
-                                         const T* __restrict__ pn) {
+                                         const T* __restrict__ pn, T sigma = T(1)) {
   const Grid3 g = d.g;
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   const T* __restrict__ q = d.q;
@@ -345,7 +350,7 @@ __device__ __forceinline__ T update_tile(const CGDesc<T>& d, long long lt, T alp
 #pragma unroll 4
     for (int k = c.z0; k < c.z1; ++k, o += g.sz) {
       const T xv = fmaT(alpha, ldv(pn + o), ldv(x + o));
-      const T rv = fmaT(-alpha, ldv(q + o), ldv(r + o));
+      const T rv = fmaT(-alpha, ldv(q + o), sigma * ldv(r + o));
       x[o] = xv;
       r[o] = rv;
       tacc = fmaT(rv, rv, tacc);
@@ -378,7 +383,7 @@ __device__ __forceinline__ double2 ldv4(const double2* p) { return __ldcg(p); }
 
 template <typename T>
 __device__ __forceinline__ double update_flat(const CGDesc<T>& d, int bl, int G, T alpha,
-                                              const T* __restrict__ pn) {
+                                              const T* __restrict__ pn, T sigma = T(1)) {
   const long long n = d.g.nodes();
   T* __restrict__ x = d.x;
   T* __restrict__ r = d.r;
@@ -406,7 +411,7 @@ __device__ __forceinline__ double update_flat(const CGDesc<T>& d, int bl, int G,
 #pragma unroll
         for (int e = 0; e < V; ++e) {
           xe[e] = fmaT(alpha, pe[e], xe[e]);
-          re[e] = fmaT(-alpha, qe[e], re[e]);
+          re[e] = fmaT(-alpha, qe[e], sigma * re[e]);
           tacc = fmaT(re[e], re[e], tacc);
         }
         *reinterpret_cast<VT*>(x + o) = xv;
@@ -415,13 +420,250 @@ __device__ __forceinline__ double update_flat(const CGDesc<T>& d, int bl, int G,
     } else {
       for (long long o = c0 + threadIdx.x; o < c1; o += kThreads) {
         const T xv = fmaT(alpha, ldv(pn + o), ldv(x + o));
-        const T rv = fmaT(-alpha, ldv(q + o), ldv(r + o));
+        const T rv = fmaT(-alpha, ldv(q + o), sigma * ldv(r + o));
         x[o] = xv;
         r[o] = rv;
         tacc = fmaT(rv, rv, tacc);
       }
     }
     acc += (double)tacc;
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------------
+// Tensor-copy staging of the float32 stencil (the MIXED inner solves).  A block's
+// stencil planes -- r and p_old of (kTX + 8) x (kTY + 2) nodes, the tile's columns with
+// a one-node halo in y and a 16-byte aligned halo of four in x -- stream through a ring
+// of kStages shared-memory stages: thread 0 issues the two cp.async.bulk.tensor copies
+// of a plane kStages planes ahead, and a "full" mbarrier per stage counts their bytes.
+// No register holds a load and no block barrier separates the planes: every thread forms
+// the nine p_new = sigma r + beta p_old values of its 3x3 neighbourhood straight from the
+// stage, each warp releases the stage through an "empty" mbarrier when it is done with
+// it, and thread 0 refills a stage once all warps have released it -- so warps drift
+// apart by up to kStages planes and hide each other's latencies.  Out-of-range boxes
+// (x < 0, y < 0, planes -1 and nz + 1, the padding columns) read as zeros.
+// ---------------------------------------------------------------------------------
+constexpr int kBoxX = kTX + 8;
+constexpr int kBoxY = kTY + 2;
+#ifndef EXCMG_TMA_STAGES
+#define EXCMG_TMA_STAGES 4
+#endif
+#ifndef EXCMG_TMA_PLANES
+#define EXCMG_TMA_PLANES 4
+#endif
+constexpr int kStages = EXCMG_TMA_STAGES;
+constexpr int kZs = EXCMG_TMA_PLANES;  // planes per copy (the box's z extent)
+constexpr unsigned kBoxBytes = kBoxX * kBoxY * kZs * sizeof(float);
+// a box's shared-memory slot, rounded up to 128 bytes so that every copy destination is
+// 128-byte aligned
+constexpr int kBoxSlot = ((kBoxBytes + 127) / 128) * 128 / sizeof(float);
+constexpr int kWarps = kThreads / 32;
+
+struct TmaRing {
+  float stage[kStages][2][kBoxSlot];      // r and p_old of kZs planes per stage (kZs x kBoxY x kBoxX)
+  unsigned long long full[kStages];       // the stage's copies have landed
+  unsigned long long empty[kStages];      // every warp is done reading the stage
+  int abort;                              // a wait ran out: the block leaves the step
+};
+static_assert(kBoxSlot * sizeof(float) % 128 == 0, "stage slots must keep 128-byte alignment");
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, P;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the barrier's phase `parity` to complete; false after wait_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity,
+                                          unsigned long long wait_ns) {
+  if (mbar_test(b, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_test(b, parity)) return true;
+    if (global_ns() - t0 > wait_ns) return false;
+  }
+}
+
+// One box of kZs planes (x, y, z .. z + kZs - 1) of a padded float32 array into shared
+// memory; its bytes complete the transaction count of barrier b.  x is a multiple of 4.
+__device__ __forceinline__ void tma_planes(float* dst, const CUtensorMap* m, unsigned long long* b,
+                                           int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(m), "r"(x), "r"(y), "r"(z), "r"(smem_u32(b))
+      : "memory");
+}
+
+// Parity bits of the ring's barriers, carried by every thread across the steps of a
+// launch (full: the next phase each stage's copies complete; empty: thread 0's record of
+// the stages' releases).
+struct RingPhases {
+  unsigned full = 0, empty = 0;
+};
+
+// The K1 body over the tiles bl, bl + G, ... of one float32 problem with tensor-copy
+// staging: p_new = sigma r + beta p_old (sigma = the folded RHS scale on the first step,
+// else 1; p_old not read on the first step), q = A p_new, and this thread's share of
+// p.q.  A tile's planes z0 - 1 .. z1 arrive kZs at a time (the last box of a tile may
+// reach past z1; those planes are not used).  A wait that runs out sets ring.abort;
+// every thread leaves its loop when it sees it, and the flag is read again after the
+// block barrier that follows the call.
+__device__ double spmv_tiles_tma(const CGDesc<float>& d, int bl, int G, bool first, float beta,
+                                 float sigma, const CUtensorMap* mr, const CUtensorMap* mp,
+                                 float* __restrict__ pnew, TmaRing& R, RingPhases& ph,
+                                 unsigned long long wait_ns) {
+  const Grid3 g = d.g;
+  const Tiling tl = d.t;
+  const long long T = tl.count();
+  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX, lane = threadIdx.x & 31;
+  float* __restrict__ q = d.q;
+  const float c0 = (float)d.A.c0, fx = (float)d.A.fx, fy = (float)d.A.fy, fz = (float)d.A.fz;
+  const float exy = (float)d.A.exy, exz = (float)d.A.exz, eyz = (float)d.A.eyz;
+  const unsigned tx_bytes = first ? kBoxBytes : 2 * kBoxBytes;
+  volatile int* abort = &R.abort;
+  // producer cursor (thread 0): tile, its origin and the first plane of the next copy;
+  // the tile's coordinates are formed once per tile
+  long long lt = bl;
+  TileXYZ lc{0, 0, 0, 0};
+  int lkk = 0;
+  if (lt < T) {
+    lc = tile_coords(g, tl, lt);
+    lkk = lc.z0 - 1;
+  }
+  int issued = 0, consumed = 0;  // boxes copied / applied in this call (thread 0's counts)
+  auto issue = [&](int slot) {
+    ++issued;
+    mbar_arrive_tx(&R.full[slot], tx_bytes);
+    tma_planes(&R.stage[slot][0][0], mr, &R.full[slot], lc.x0 - 4, lc.y0 - 1, lkk);
+    if (!first) tma_planes(&R.stage[slot][1][0], mp, &R.full[slot], lc.x0 - 4, lc.y0 - 1, lkk);
+    lkk += kZs;
+    if (lkk > lc.z1) {
+      lt += G;
+      if (lt < T) {
+        lc = tile_coords(g, tl, lt);
+        lkk = lc.z0 - 1;
+      }
+    }
+  };
+  if (threadIdx.x == 0)
+    for (int st = 0; st < kStages && lt < T; ++st) issue(st);
+  int slot = 0;
+  double acc = 0.0;
+  bool stop = false;
+  // this thread's 3x3 neighbourhood in a plane of a stage: rows ty .. ty + 2, columns
+  // tx + 3 .. tx + 5 (stage column c holds x = x0 - 4 + c)
+  const int base = ty * kBoxX + tx + 3;
+  for (long long t = bl; t < T && !stop; t += G) {
+    const TileXYZ c = tile_coords(g, tl, t);
+    const int i = c.x0 + tx, j = c.y0 + ty;
+    const bool own = (i < g.sy) && (j <= g.ny);
+    const bool inxy = (i > 0) && (i < g.nx) && (j > 0) && (j < g.ny);
+    float Pm1 = 0.f, Cm1 = 0.f, Tm1 = 0.f, Tm2 = 0.f, tacc = 0.f;
+    for (int k0 = c.z0 - 1; k0 <= c.z1; k0 += kZs) {
+      if (!mbar_wait(&R.full[slot], (ph.full >> slot) & 1u, wait_ns)) *abort = 1;
+      ph.full ^= 1u << slot;
+      if (*abort) {
+        stop = true;
+        break;
+      }
+      const int np = min(kZs, c.z1 + 1 - k0);  // planes of this box that the tile uses
+#pragma unroll 1
+      for (int pz = 0; pz < kZs; ++pz) {
+        if (pz < np) {
+          const float* rs = &R.stage[slot][0][pz * kBoxY * kBoxX + base];
+          const float* ps = &R.stage[slot][1][pz * kBoxY * kBoxX + base];
+          float v[3][3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+              v[a][b] = first ? sigma * rs[a * kBoxX + b] : fmaf(beta, ps[a * kBoxX + b], rs[a * kBoxX + b]);
+          const float P = v[1][1];
+          const float SX = v[1][0] + v[1][2];
+          const float SY = v[0][1] + v[2][1];
+          const float EXY = (v[0][0] + v[0][2]) + (v[2][0] + v[2][2]);
+          const float Ck = fmaf(c0, P, fmaf(fx, SX, fmaf(fy, SY, exy * EXY)));
+          const float Tk = fmaf(fz, P, fmaf(exz, SX, eyz * SY));
+          const int kc = k0 + pz - 1;
+          if (kc >= c.z0 && own) {
+            const long long o = i + j * g.sy + (long long)kc * g.sz;
+            const bool interior = inxy && kc > 0 && kc < g.nz;
+            const float qv = interior ? (Cm1 + Tm2) + Tk : 0.f;
+            pnew[o] = Pm1;
+            q[o] = qv;
+            tacc = fmaf(Pm1, qv, tacc);
+          }
+          Tm2 = Tm1;
+          Tm1 = Tk;
+          Cm1 = Ck;
+          Pm1 = P;
+        }
+      }
+      // the stage is read: this warp releases it
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&R.empty[slot]);
+      if (threadIdx.x == 0) {
+        ++consumed;
+        // refill this stage with the box kStages ahead once every warp has released it
+        if (lt < T) {
+          if (!mbar_wait(&R.empty[slot], (ph.empty >> slot) & 1u, wait_ns)) *abort = 1;
+          ph.empty ^= 1u << slot;
+          if (!*abort) issue(slot);
+        }
+      }
+      slot = slot + 1 == kStages ? 0 : slot + 1;
+    }
+    acc += (double)tacc;
+  }
+  if (threadIdx.x == 0) {
+    // the releases of the last boxes' stages (no refill waited for them), then, after a
+    // wait that ran out, the copies still in flight: nothing lands in shared memory or
+    // is left half-counted once the block moves on
+    const int tail = issued < kStages ? issued : kStages;
+    int s0 = (consumed - tail) % kStages;
+    if (s0 < 0) s0 += kStages;
+    for (int n = 0; n < tail && !stop; ++n) {
+      const int st = (s0 + n) % kStages;
+      if (!mbar_wait(&R.empty[st], (ph.empty >> st) & 1u, wait_ns)) *abort = 1;
+      ph.empty ^= 1u << st;
+    }
+    if (stop || *abort) {
+      for (int n = consumed; n < issued; ++n) {
+        mbar_wait(&R.full[slot], (ph.full >> slot) & 1u, wait_ns);
+        ph.full ^= 1u << slot;
+        slot = slot + 1 == kStages ? 0 : slot + 1;
+      }
+    }
   }
   return acc;
 }
@@ -517,9 +759,9 @@ __global__ void __launch_bounds__(kThreads)
 // second barrier or broadcast is needed.  Barrier waits are bounded: on time-out the
 // kernel records EXCMG_ERR_TIMEOUT and returns.
 // ---------------------------------------------------------------------------------
-// polls before a barrier wait gives up: several seconds with the back-off (a team's first
-// barrier may wait for members still finishing another problem)
-constexpr unsigned long long kSpinLimit = 1ull << 25;
+// Every wait of a cooperative CG launch gives up after wait_ns nanoseconds of the
+// global timer (default 20 s: a team's first barrier may wait for members still
+// finishing another problem of a batch).
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -527,8 +769,9 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-// Every block arrives once; returns false in every block that saw a time-out.
-__device__ bool grid_barrier(unsigned* bar, unsigned target, int* err) {
+// Every block arrives once; returns false in every block that saw a time-out (its own
+// wait ran out after wait_ns, or another block's did: the shared error flag).
+__device__ bool grid_barrier(unsigned* bar, unsigned target, int* err, unsigned long long wait_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -536,13 +779,21 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* err) {
     // visible before the arrival; the acquire loads below see every other block's
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     int ok = 1;
-    unsigned long long spins = 0;
+    unsigned spins = 0;
+    unsigned long long t0 = 0;
     while (ld_acquire(bar) < target) {
-      if (++spins > kSpinLimit || *(volatile int*)err) {
+      if (*(volatile int*)err) {
         ok = 0;
         break;
       }
-      if (spins > 4096) __nanosleep(64);  // tight polling first, back off on long waits
+      if (++spins == 4096) t0 = global_ns();
+      if (spins > 4096) {  // tight polling first, then back off and watch the clock
+        if (global_ns() - t0 > wait_ns) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
     }
     if (!ok) atomicExch(err, 1);
     s_ok = ok;
@@ -562,13 +813,15 @@ __device__ double sum_partials_all(const double* part, int n) {
 #endif
 
 // The CG loop of one problem, run by the G = d.blk_count blocks of its team (this block
-// is member bl).
-template <typename T>
-__device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* partials,
-                        unsigned* bars, T (*sp)[kTY + 2][kTX + 2], double& s_scalar, int& buf) {
+// is member bl).  kTma: the float32 engine whose K1 body stages its planes by tensor
+// copies (ring R); returns true if the ring was abandoned after a wait ran out.
+template <typename T, bool kTma>
+__device__ bool cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* partials,
+                        unsigned* bars, T (*sp)[kTY + 2][kTX + 2], double& s_scalar, int& buf,
+                        TmaRing* R, RingPhases& phases, unsigned long long wait_ns) {
   const int G = d.blk_count;
   CGState* S = st + d.slot;
-  if (S->done) return;  // same value in every block of this team
+  if (S->done) return false;  // same value in every block of this team
   const long long total_tiles = d.t.count();
   double* partA = partials + (long long)p * 2 * kMaxGrid;
   double* partB = partA + G;
@@ -578,7 +831,15 @@ __device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* 
   int iter = S->iter;
   const int max_iter = S->max_iter, fixed = S->fixed;
   bool first = S->first != 0;
+  // MIXED: the right-hand side is scaled inside the first step (r <- scale r), so the
+  // state's r.r and tolerance scale by scale^2 here
+  const bool fold = first && d.fold_scale;
+  if (fold) {
+    rr *= d.scale * d.scale;
+    tol2 *= d.scale * d.scale;
+  }
   int status = EXCMG_OK;
+  bool broken = false;
   unsigned nbar = 0;
   // a team of one block needs no grid barrier, only the block's own
   auto sync_all = [&]() -> bool {
@@ -586,15 +847,28 @@ __device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* 
       __syncthreads();
       return true;
     }
-    return grid_barrier(bar, ++nbar * (unsigned)G, err);
+    return grid_barrier(bar, ++nbar * (unsigned)G, err, wait_ns);
   };
   for (;;) {
+    const T sigma = (first && fold) ? (T)d.scale : T(1);
     // K1 body
     const T* pold = (iter & 1) ? d.pb : d.pa;
     T* pnew = (iter & 1) ? d.pa : d.pb;
     double acc = 0.0;
-    for (long long t = bl; t < total_tiles; t += G)
-      acc += (double)spmv_tile<T>(d, t, first, (T)beta, pold, pnew, sp, buf);
+    if constexpr (kTma) {
+      const CUtensorMap* mp = (iter & 1) ? &d.tm->pb : &d.tm->pa;
+      acc = spmv_tiles_tma(d, bl, G, first, (float)beta, sigma, &d.tm->r, mp, pnew, *R, phases, wait_ns);
+      __syncthreads();
+      if (R->abort) {  // uniform: read after the block barrier
+        broken = true;
+        status = EXCMG_ERR_TIMEOUT;
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        break;
+      }
+    } else {
+      for (long long t = bl; t < total_tiles; t += G)
+        acc += (double)spmv_tile<T>(d, t, first, (T)beta, pold, pnew, sp, buf);
+    }
     double bs = block_sum(acc);
     if (threadIdx.x == 0) partA[bl] = bs;
     if (!sync_all()) {
@@ -616,16 +890,23 @@ __device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* 
     // (every block busy, one short column each -- lower latency)
     acc = 0.0;
     if (d.g.nodes() >= (long long)G * kChunk) {
-      acc = update_flat<T>(d, bl, G, (T)alpha, pnew);
+      acc = update_flat<T>(d, bl, G, (T)alpha, pnew, sigma);
     } else {
-      for (long long t = bl; t < total_tiles; t += G) acc += (double)update_tile<T>(d, t, (T)alpha, pnew);
+      for (long long t = bl; t < total_tiles; t += G)
+        acc += (double)update_tile<T>(d, t, (T)alpha, pnew, sigma);
     }
     bs = block_sum(acc);
     if (threadIdx.x == 0) partB[bl] = bs;
+    if (kTma) {
+      // the next step's tensor copies (async proxy) read r and p written here and by the
+      // other blocks (generic proxy): order them after the grid barrier's acquire
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
     if (!sync_all()) {
       status = EXCMG_ERR_TIMEOUT;
       break;
     }
+    if (kTma) asm volatile("fence.proxy.async.global;" ::: "memory");
     bs = sum_partials_all(partB, G);
     if (threadIdx.x == 0) s_scalar = bs;
     __syncthreads();
@@ -655,6 +936,7 @@ __device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* 
     S->status = status;
     S->done = 1;
   }
+  return broken;
 }
 
 // Blocks form one team per problem: each block takes the next slot from an atomic
@@ -662,17 +944,49 @@ __device__ void cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* 
 // are handed out in order, so at most one team is ever partly formed and every earlier
 // team finishes and frees its blocks: a team whose members arrive late only waits.
 // A block whose team is done takes the next slot; a block past the last slot exits.
-template <typename T>
-__global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
+// kTma (float32 only): K1 stages its stencil planes by tensor copies.
+#ifndef EXCMG_PERSIST_TMA_MIN_BLOCKS
+#define EXCMG_PERSIST_TMA_MIN_BLOCKS 2
+#endif
+template <typename T, bool kTma>
+__global__ void __launch_bounds__(kThreads, kTma ? EXCMG_PERSIST_TMA_MIN_BLOCKS : EXCMG_PERSIST_MIN_BLOCKS)
     k_cg_persistent(int nprob, const CGDesc<T>* __restrict__ descs, CGState* st,
-                    double* partials, unsigned* bars) {
-  __shared__ T sp[2][kTY + 2][kTX + 2];
+                    double* partials, unsigned* bars, unsigned long long wait_ns) {
   __shared__ double s_scalar;
   __shared__ int s_slot;
+  T(*sp)[kTY + 2][kTX + 2] = nullptr;
+  TmaRing* R = nullptr;
+  if constexpr (kTma) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];  // sizeof(TmaRing) bytes
+    TmaRing& ring = *reinterpret_cast<TmaRing*>(dyn_smem);
+    R = &ring;
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < kStages; ++k) {
+        mbar_init(&ring.full[k], 1);
+        mbar_init(&ring.empty[k], kWarps);
+      }
+      ring.abort = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      // the tensor maps were copied to global memory before the launch
+      for (int q = 0; q < nprob; ++q) {
+        const TmapSet* m = descs[q].tm;
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m->r) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m->pa) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&m->pb) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&m->r) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&m->pa) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&m->pb) : "memory");
+      }
+    }
+  } else {
+    __shared__ T stage[2][kTY + 2][kTX + 2];
+    sp = stage;
+  }
   unsigned* slot_counter = bars + 2 * nprob;
   int total_slots = 0;
   for (int q = 0; q < nprob; ++q) total_slots = max(total_slots, descs[q].blk_begin + descs[q].blk_count);
   int buf = 0;
+  RingPhases phases;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_slot = (int)atomicAdd(slot_counter, 1u);
@@ -682,7 +996,9 @@ __global__ void __launch_bounds__(kThreads, EXCMG_PERSIST_MIN_BLOCKS)
     int p = 0;
     while (p < nprob && !(slot >= descs[p].blk_begin && slot < descs[p].blk_begin + descs[p].blk_count)) ++p;
     if (p >= nprob) return;  // unreachable: every slot below total_slots has a team
-    cg_team<T>(descs[p], p, slot - descs[p].blk_begin, st, partials, bars, sp, s_scalar, buf);
+    if (cg_team<T, kTma>(descs[p], p, slot - descs[p].blk_begin, st, partials, bars, sp, s_scalar,
+                         buf, R, phases, wait_ns))
+      return;  // the copy ring was abandoned: this block takes no further work
   }
 }
 
@@ -750,6 +1066,20 @@ __device__ __forceinline__ double res_rhs2(const ResDesc& d, int i, int j, int k
                                   (F.at(i, j, k - 1) + F.at(i, j, k + 1))));
 }
 
+// The residual's block sums of one problem (r.r, ||b||^2 with the lift, ||RHS(f)||^2)
+// added to its three partials in shared memory.  Called at problem switches only; kept
+// out of line so that it adds no registers to the plane loop.
+__device__ __noinline__ void residual_flush(double acc_r, double acc_b, double acc_b4, double* part) {
+  const double s1 = block_sum(acc_r);
+  const double s2 = block_sum(fma(0.25, acc_b4, acc_b));
+  const double s3 = block_sum(0.25 * acc_b4);
+  if (threadIdx.x == 0) {
+    part[0] += s1;
+    part[1] += s2;
+    part[2] += s3;
+  }
+}
+
 // Each thread marches its kResRows rows of one x-column through the tile's planes.  Per
 // plane it loads the (kResRows + 2) x 3 neighbourhood (through the read-only cache:
 // neighbouring threads share the lines; no staging, no block barrier) and forms, per row,
@@ -770,28 +1100,26 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
   constexpr int R = kResRows;
   static_assert(kTX == 32, "one warp per x-run of a residual tile row");
   __shared__ int s_active[kMaxProb];
-  __shared__ double s_part[2 * kMaxProb];
+  __shared__ double s_part[3 * kMaxProb];
   for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
     s_active[p] = 1;
-    s_part[2 * p] = 0.0;
-    s_part[2 * p + 1] = 0.0;
+    s_part[3 * p] = 0.0;
+    s_part[3 * p + 1] = 0.0;
+    s_part[3 * p + 2] = 0.0;
   }
   __syncthreads();
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   int cur = -1, p = 0;
-  // acc_b4 sums (2 b)^2 over nodes whose stencil misses the boundary (there b = -RHS)
+  // acc_b4 sums (2 RHS)^2 over every interior node: ||RHS(f)||^2 = acc_b4 / 4 is the
+  // forcing reading of ||f_h||.  b = -RHS - lift, and the lift is nonzero only next to
+  // the boundary, so ||b||^2 = acc_b4 / 4 + acc_b with acc_b summing b^2 - RHS^2 =
+  // lift (lift + 2 RHS) over those nodes (the lift reading).
   double acc_r = 0.0, acc_b = 0.0, acc_b4 = 0.0;
+  auto flush = [&](int q) { residual_flush(acc_r, acc_b, acc_b4, s_part + 3 * q); };
   for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
     p = find_problem(descs, nprob, t, p);
     if (p != cur) {
-      if (cur >= 0) {
-        const double s1 = block_sum(acc_r);
-        const double s2 = block_sum(fma(0.25, acc_b4, acc_b));
-        if (threadIdx.x == 0) {
-          s_part[2 * cur] += s1;
-          s_part[2 * cur + 1] += s2;
-        }
-      }
+      if (cur >= 0) flush(cur);
       acc_r = acc_b = acc_b4 = 0.0;
       cur = p;
     }
@@ -799,6 +1127,8 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
     const Grid3 g = d.g;
     const double* __restrict__ u = d.u;
     TR* __restrict__ rout = reinterpret_cast<TR*>(d.r);
+    // output strides: the padded float32 layout, or the grid's own for float64
+    const long long osy = sizeof(TR) == 4 ? d.osy : g.sy, osz = sizeof(TR) == 4 ? d.osz : g.sz;
     const TileXYZ c = res_tile_coords(g, d.t, t - d.tile_begin);
     const int i = c.x0 + tx, jb = c.y0 + R * ty;  // rows jb .. jb + R - 1
     if (c.x0 >= g.nx || c.y0 >= g.ny || c.z0 >= g.nz) {
@@ -808,7 +1138,7 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
 #pragma unroll
         for (int q = 0; q < R; ++q) {
           const int j = jb + q;
-          if (i <= g.nx && j <= g.ny) rout[i + j * g.sy + (long long)kc * g.sz] = (TR)0.0;
+          if (i < osy && j <= g.ny) rout[i + j * osy + (long long)kc * osz] = (TR)0.0;
         }
       continue;
     }
@@ -855,18 +1185,18 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
             rv = fma(-0.5, rhs2, -((Cm1[q] + Tm2[q]) + Tk));
             acc_r = fma(rv, rv, acc_r);
             if (want_b) {
+              acc_b4 = fma(rhs2, rhs2, acc_b4);
               const bool yface = (j == 1 || j == g.ny - 1), xface = (i == 1 || i == g.nx - 1);
-              if (!yface && !xface && kc >= 2 && kc <= g.nz - 2) {
-                acc_b4 = fma(rhs2, rhs2, acc_b4);  // b = -RHS here
-              } else if (yface || !xface) {
+              if ((yface || !xface) && (yface || kc < 2 || kc > g.nz - 2)) {
                 const double lift = yface ? perim_lift(u, g, A, i, j, kc)
                                           : (kc == 1 ? Tm2[q] : 0.0) + (kc == g.nz - 1 ? Tk : 0.0);
-                const double bv = fma(-0.5, rhs2, -lift);
-                acc_b = fma(bv, bv, acc_b);
-              }  // else next to an x face only: after the plane loop
+                acc_b = fma(lift, lift + rhs2, acc_b);
+              }  // next to an x face only: after the plane loop; elsewhere b = -RHS
             }
           }
-          rout[o] = (TR)rv;
+          rout[i + j * osy + (long long)kc * osz] = (TR)rv;
+        } else if (sizeof(TR) == 4 && kc >= c.z0 && i > g.nx && i < osy && j <= g.ny) {
+          rout[i + j * osy + (long long)kc * osz] = (TR)0.0;  // padding column
         }
         Tm2[q] = Tm1[q];
         Tm1[q] = Tk;
@@ -891,43 +1221,56 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
             const int kc = k0 + lane;
             if (kc < k_hi) {
               const long long o = xi + j * g.sy + (long long)kc * g.sz;
-              const double bv = fma(-0.5, res_rhs2(d, xi, j, kc, o), -perim_lift(u, g, A, xi, j, kc));
-              acc_b = fma(bv, bv, acc_b);
+              const double lift = perim_lift(u, g, A, xi, j, kc);
+              acc_b = fma(lift, lift + res_rhs2(d, xi, j, kc, o), acc_b);
             }
           }
         }
       }
     }
   }
-  if (cur >= 0) {
-    const double s1 = block_sum(acc_r);
-    const double s2 = block_sum(fma(0.25, acc_b4, acc_b));
-    if (threadIdx.x == 0) {
-      s_part[2 * cur] += s1;
-      s_part[2 * cur + 1] += s2;
-    }
-  }
+  if (cur >= 0) flush(cur);
   __syncthreads();
-  publish_and_finish<2>(nprob, s_active, s_part, partials, counters, FinRes{descs, st});
+  publish_and_finish<3>(nprob, s_active, s_part, partials, counters, FinRes{descs, st});
 }
 
-// MIXED refinement: u += e (float32 correction), then e = 0 for the next inner solve.
+// MIXED refinement: u += e / scale (the float32 correction of the scaled system), then
+// e = 0 for the next inner solve.  e has the padded float32 layout, u the float64 one;
+// a warp walks one row (j, k) at a time, lanes along x, four elements in flight each.
 __global__ void __launch_bounds__(kThreads)
-    k_add_correction(int nprob, const CGDesc<float>* __restrict__ descs, long long total_tiles) {
-  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-  int p = 0;
-  for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-    p = find_problem(descs, nprob, t, p);
+    k_add_correction(int nprob, const CGDesc<float>* __restrict__ descs) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * kThreads) >> 5;
+  for (int p = 0; p < nprob; ++p) {
     const CGDesc<float>& d = descs[p];
     const Grid3 g = d.g;
-    const TileXYZ c = tile_coords(g, d.t, t - d.tile_begin);
-    const int i = c.x0 + tx, j = c.y0 + ty;
-    if (i > g.nx || j > g.ny) continue;
-    long long o = i + j * g.sy + (long long)c.z0 * g.sz;
+    const long long rows = (long long)(g.ny + 1) * (g.nz + 1);
     const double inv = 1.0 / d.scale;
-    for (int k = c.z0; k < c.z1; ++k, o += g.sz) {
-      d.aux[o] += (double)d.x[o] * inv;
-      d.x[o] = 0.0f;
+    float* __restrict__ e = d.x;
+    double* __restrict__ u = d.aux;
+    for (long long row = warp; row < rows; row += nwarps) {
+      const long long j = row % (g.ny + 1), k = row / (g.ny + 1);
+      float* er = e + j * g.sy + k * g.sz;
+      double* ur = u + j * d.aux_sy + k * d.aux_sz;
+      for (int i0 = 0; i0 <= g.nx; i0 += 4 * 32) {
+        float ev[4];
+        double uv[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = i0 + m * 32 + lane;
+          ev[m] = i <= g.nx ? __ldcs(er + i) : 0.f;
+          uv[m] = i <= g.nx ? __ldcs(ur + i) : 0.0;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = i0 + m * 32 + lane;
+          if (i <= g.nx) {
+            __stcs(ur + i, fma((double)ev[m], inv, uv[m]));
+            __stcs(er + i, 0.f);
+          }
+        }
+      }
     }
   }
 }
@@ -960,36 +1303,101 @@ __global__ void __launch_bounds__(kThreads)
 
 int g_max_grid = 0;
 int g_coop_grid[2] = {0, 0};  // co-resident blocks of k_cg_persistent<double>, <float>
+int g_coop_grid_tma = 0;      // the same for the float32 tensor-copy engine
 
 }  // namespace
 
-template <typename T>
-int persistent_cg_blocks() {
-  int& cached = g_coop_grid[sizeof(T) == 8 ? 0 : 1];
+// Dynamic shared memory of a k_cg_persistent launch (the tensor-copy ring).
+template <bool kTma>
+size_t persistent_smem() {
+  return kTma ? sizeof(TmaRing) : 0;
+}
+
+template <typename T, bool kTma>
+int coop_blocks(int& cached) {
   if (cached == 0) {
     int dev = 0, sms = 0, occ = 0, coop = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_persistent<T>, kThreads, 0);
+    if (kTma)
+      cudaFuncSetAttribute(k_cg_persistent<T, kTma>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)persistent_smem<kTma>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_persistent<T, kTma>, kThreads,
+                                                  persistent_smem<kTma>());
     cached = (coop && sms > 0 && occ > 0) ? std::min(sms * occ, kMaxGrid) : -1;
   }
   return cached;
 }
+
+template <typename T>
+int persistent_cg_blocks() {
+  return coop_blocks<T, false>(g_coop_grid[sizeof(T) == 8 ? 0 : 1]);
+}
 template int persistent_cg_blocks<double>();
 template int persistent_cg_blocks<float>();
 
+int persistent_cg_blocks_tma() { return coop_blocks<float, true>(g_coop_grid_tma); }
+
 template <typename T>
 cudaError_t launch_cg_persistent(int nprob, const CGDesc<T>* descs, int grid, CGState* st,
-                                 double* partials, unsigned* bar, cudaStream_t s) {
-  void* args[] = {(void*)&nprob, (void*)&descs, (void*)&st, (void*)&partials, (void*)&bar};
-  return cudaLaunchCooperativeKernel((const void*)k_cg_persistent<T>, dim3(grid), dim3(kThreads),
-                                     args, 0, s);
+                                 double* partials, unsigned* bar, unsigned long long wait_ns,
+                                 bool tma, cudaStream_t s) {
+  void* args[] = {(void*)&nprob, (void*)&descs, (void*)&st, (void*)&partials, (void*)&bar,
+                  (void*)&wait_ns};
+  const void* fn = (const void*)k_cg_persistent<T, false>;
+  size_t smem = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (tma) {
+      fn = (const void*)k_cg_persistent<float, true>;
+      smem = persistent_smem<true>();
+    }
+  }
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
 }
 template cudaError_t launch_cg_persistent<double>(int, const CGDesc<double>*, int, CGState*, double*,
-                                                  unsigned*, cudaStream_t);
+                                                  unsigned*, unsigned long long, bool, cudaStream_t);
 template cudaError_t launch_cg_persistent<float>(int, const CGDesc<float>*, int, CGState*, double*,
-                                                 unsigned*, cudaStream_t);
+                                                 unsigned*, unsigned long long, bool, cudaStream_t);
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int tma_slab_depth(int tz) {
+  // the slab depth nearest tz whose tz + 2 planes are whole copies of kZs planes
+  if (tz + 2 <= kZs) return kZs - 2 > 0 ? kZs - 2 : tz;
+  const int lo = ((tz + 2) / kZs) * kZs - 2, hi = lo + kZs;
+  return (tz - lo <= hi - tz) ? lo : hi;
+}
+
+bool encode_plane_map(CUtensorMap* m, float* base, const Grid3& g32) {
+  static EncodeTiledFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  if (!fn) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (g32.sy & 3)) return false;
+  // x extent nx + 1: the padding columns are outside the map and read as zeros
+  const cuuint64_t dims[3] = {(cuuint64_t)g32.nx + 1, (cuuint64_t)g32.ny + 1, (cuuint64_t)g32.nz + 1};
+  const cuuint64_t strides[2] = {(cuuint64_t)g32.sy * sizeof(float), (cuuint64_t)g32.sz * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)kBoxX, (cuuint32_t)kBoxY, (cuuint32_t)kZs};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 int persistent_grid(long long total_tiles) {
   if (g_max_grid == 0) {
@@ -1017,7 +1425,8 @@ int residual_grid(long long total_tiles) {
     if (sms <= 0) sms = 1;
     if (occ <= 0) occ = 1;
     g_res_grid = sms * occ;
-    if (g_res_grid > kMaxGrid) g_res_grid = kMaxGrid;
+    // the residual publishes 3 partials per block into room for 2 x kMaxGrid
+    if (g_res_grid > 2 * kMaxGrid / 3) g_res_grid = 2 * kMaxGrid / 3;
   }
   long long g = total_tiles < g_res_grid ? total_tiles : g_res_grid;
   return g < 1 ? 1 : (int)g;
@@ -1053,7 +1462,17 @@ cudaError_t launch_residual(bool out_float, int nprob, const ResDesc* descs, lon
 
 cudaError_t launch_add_correction(int nprob, const CGDesc<float>* inner, long long total_tiles,
                                   int grid, cudaStream_t s) {
-  k_add_correction<<<grid, kThreads, 0, s>>>(nprob, inner, total_tiles);
+  (void)total_tiles;
+  (void)grid;
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_add_correction, kThreads, 0);
+    blocks = std::max(1, sms) * std::max(1, occ);
+  }
+  k_add_correction<<<blocks, kThreads, 0, s>>>(nprob, inner);
   return cudaGetLastError();
 }
 

@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kDsThreads)
   auto ub = [&](int i, int j, int k) -> double {
     return (i == 0 || i == g.nx || j == 0 || j == g.ny || k == 0 || k == g.nz) ? d.gb.at(i, j, k) : 0.0;
   };
-  double acc_b = 0.0;
+  double acc_b = 0.0, acc_f4 = 0.0;  // ||b||^2 and ||2 RHS(f)||^2: the readings of ||f_h||
   for (int t = threadIdx.x; t < n; t += kDsThreads) {
     const int i = t % mx + 1, j = (t / mx) % my + 1, k = t / (mx * my) + 1;
     const View& F = d.f;
@@ -131,8 +131,12 @@ __global__ void __launch_bounds__(kDsThreads)
     V[t] = b;
     Bv[t] = b;
     acc_b = fma(b, b, acc_b);
+    acc_f4 = fma(rhs2, rhs2, acc_f4);
   }
-  const double bb = ds_block_sum(acc_b, s_park);
+  const double bb_lift = ds_block_sum(acc_b, s_park);
+  __syncthreads();
+  const double bb_force = 0.25 * ds_block_sum(acc_f4, s_park);
+  const double bb = (d.forcing && bb_force > 0.0) ? bb_force : bb_lift;
   __syncthreads();
   ds_axis(V, W, Sx, mx, my, mz, 0);
   __syncthreads();

@@ -25,6 +25,13 @@ Grid3 make_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz) {
   return g;
 }
 
+Grid3 padded_f32(const Grid3& g) {
+  Grid3 p = g;
+  p.sy = (g.nx + 1 + 3) & ~3LL;
+  p.sz = p.sy * (g.ny + 1);
+  return p;
+}
+
 Coef make_coef(const Grid3& g) {
   const double a = 1.0 / (g.hx * g.hx), b = 1.0 / (g.hy * g.hy), c = 1.0 / (g.hz * g.hz);
   Coef A;
@@ -157,8 +164,18 @@ bool options_ok(const excmg_options* o) {
       o->prolong != EXCMG_PROLONG_LINEAR)
     return false;
   if (o->history && (o->history_len < 1 || o->precision != EXCMG_FP64)) return false;
+  if (o->rhs_norm != EXCMG_RHS_NORM_LIFT && o->rhs_norm != EXCMG_RHS_NORM_FORCING) return false;
+  if (!(o->wait_timeout_ms >= 0) || !std::isfinite(o->wait_timeout_ms) || o->wait_timeout_ms > 3.6e6)
+    return false;
+  if (o->test_phantom_blocks < 0 || o->test_phantom_blocks > 64) return false;
   return true;
 }
+
+}  // namespace
+
+bool excmg::options_valid(const excmg_options* o) { return options_ok(o); }
+
+namespace {
 
 // Per-problem workspace layout.
 struct ProbLayout {
@@ -184,6 +201,8 @@ ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_
     off = align_up(off + sizeof(double) * lv[l].nodes());
   }
   const long long nf = lv.back().nodes();
+  // float32 vectors use the padded row pitch (padded_f32): nodes of the finest level
+  const long long nf32 = (long long)((lv.back().nx + 1 + 3) & ~3) * (lv.back().ny + 1) * (lv.back().nz + 1);
   // float64 CG vectors: every level (FP64), or the levels MIXED solves in float64
   long long n64 = 0;
   for (size_t k = 0; k < lv.size(); ++k)  // (levels 0 and 1: DSOLVE works in float64)
@@ -211,15 +230,15 @@ ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_
   }
   if (mixed) {
     L.r32 = off;
-    off = align_up(off + sizeof(float) * nf);
+    off = align_up(off + sizeof(float) * nf32);
     L.pa32 = off;
-    off = align_up(off + sizeof(float) * nf);
+    off = align_up(off + sizeof(float) * nf32);
     L.pb32 = off;
-    off = align_up(off + sizeof(float) * nf);
+    off = align_up(off + sizeof(float) * nf32);
     L.q32 = off;
-    off = align_up(off + sizeof(float) * nf);
+    off = align_up(off + sizeof(float) * nf32);
     L.e32 = off;
-    off = align_up(off + sizeof(float) * nf);
+    off = align_up(off + sizeof(float) * nf32);
     L.rhs64 = off;
     off = align_up(off + sizeof(double) * nf);
   }
@@ -229,7 +248,7 @@ ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_
 
 // Common header of every workspace: states, counters, partials, descriptor tables.
 struct Header {
-  size_t st, counters, bar, partials, cgd, cgf, resd, prold;
+  size_t st, counters, bar, partials, cgd, cgf, resd, prold, tmaps;
   size_t bytes;
 };
 
@@ -256,6 +275,8 @@ Header header_layout(int nprob) {
   off = align_up(off + sizeof(ResDesc) * nprob);
   H.prold = off;
   off = align_up(off + sizeof(ProlongDesc) * nprob);
+  H.tmaps = off;
+  off = align_up(off + sizeof(TmapSet) * nprob);
   H.bytes = off;
   return H;
 }
@@ -346,6 +367,8 @@ struct Ctx {
   Prof* prof = nullptr;           // set when the call is profiled
   bool persistent_ok = false;     // single-problem CG may use the cooperative kernel
   bool defer = false;             // the caller reads the CG states after the whole call
+  unsigned long long wait_ns = 20000000000ull;  // bound of every device-side wait
+  int phantom = 0;                // test only: never-launched members per cooperative team
   // Bracket one launch: record an event before `fn` and after it.
   template <typename F>
   cudaError_t timed(int kind, double nodes, F fn) const {
@@ -367,6 +390,12 @@ struct Ctx {
   CGDesc<float>* cgf() const { return reinterpret_cast<CGDesc<float>*>(ws + H.cgf); }
   ResDesc* resd() const { return reinterpret_cast<ResDesc*>(ws + H.resd); }
   ProlongDesc* prold() const { return reinterpret_cast<ProlongDesc*>(ws + H.prold); }
+  TmapSet* tmaps() const { return reinterpret_cast<TmapSet*>(ws + H.tmaps); }
+  // the wait bound and test option of `o`
+  void set_waits(const excmg_options* o) {
+    if (o->wait_timeout_ms > 0) wait_ns = (unsigned long long)(o->wait_timeout_ms * 1e6);
+    phantom = o->test_phantom_blocks;
+  }
 };
 
 // options.history: the device copy at the end of the workspace
@@ -448,9 +477,14 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
       return e;
     }
   }
+  // MIXED inner solves (float32): the tensor-copy engine when every problem has its
+  // maps; it also applies the right-hand side's scale inside its first step.  Every
+  // other engine gets the scale from k_scale_rhs first.
+  // The small grids of the phase run in one cluster each when all of them fit one.
+  int csize = 0;
+  size_t csmem = 0;
+  long long cmax = 0;
   if (coop >= n && coop > 0 && c.persistent_ok) {
-    int csize = 0;
-    size_t csmem = 0;
     for (int p = 0; p < n; ++p) {
       const int cp = hd[p].g.nodes() <= kClusterMaxNodes ? cluster_cg_size<T>(hd[p].g) : 0;
       if (cp == 0) {
@@ -459,12 +493,31 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
       }
       csize = std::max(csize, cp);
     }
-    long long cmax = 0;
     for (int p = 0; p < n && csize > 0; ++p) {
       csmem = std::max(csmem, cluster_cg_smem(hd[p].g, csize, sizeof(T)));
       cmax = std::max(cmax, hd[p].g.nodes());
     }
-    const bool small = csize > 0;
+  }
+  const bool small = csize > 0;
+  bool tma = false;
+  int coop_used = coop;
+  if constexpr (sizeof(T) == 4) {
+    bool all = c.persistent_ok && coop >= n && coop > 0 && !small;
+    for (int p = 0; p < n && all; ++p) all = hd[p].tm != nullptr;
+    const int ct = all ? persistent_cg_blocks_tma() : -1;
+    tma = all && ct >= n;
+    if (tma) coop_used = ct;
+    bool pending = false;
+    for (int p = 0; p < n; ++p) {
+      pending = pending || hd[p].fold_scale;
+      if (!tma) hd[p].fold_scale = 0;
+    }
+    if (pending && !tma) {
+      CK(cudaMemcpyAsync(ddesc, hd.data(), sizeof(CGDesc<T>) * n, cudaMemcpyHostToDevice, c.s));
+      CK(c.timed(EXCMG_K_CORRECT, nodes, [&] { return launch_scale_rhs(n, ddesc, tiles, grid, c.st(), c.s); }));
+    }
+  }
+  if (coop >= n && coop > 0 && c.persistent_ok) {
     int grid_total = 0;
     if (!small) {
       // team sizes: a lone problem takes every co-resident block it can use; in a batch
@@ -475,7 +528,7 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
       for (int p = 0; p < n; ++p) {
         const long long tp = hd[p].t.count();
         const long long want = (n == 1) ? tp : (tp + 1) / 2;
-        g[p] = (int)std::max(1LL, std::min<long long>(want, coop));
+        g[p] = (int)std::max(1LL, std::min<long long>(want, coop_used));
         order[p] = p;
         slots += g[p];
       }
@@ -483,16 +536,18 @@ excmg_status cg_loop(const Ctx& c, int n, CGDesc<T>* ddesc, long long tiles, int
       int begin = 0;
       for (int p : order) {
         hd[p].blk_begin = begin;
-        hd[p].blk_count = g[p];
-        begin += g[p];
+        // test only: members that are never launched, so the team's barriers cannot
+        // complete and its waits run out (options.test_phantom_blocks)
+        hd[p].blk_count = g[p] + c.phantom;
+        begin += g[p] + c.phantom;
       }
-      grid_total = (int)std::min<long long>(slots, coop);
+      grid_total = (int)std::min<long long>(slots, coop_used);
       CK(cudaMemcpyAsync(ddesc, hd.data(), sizeof(CGDesc<T>) * n, cudaMemcpyHostToDevice, c.s));
       CK(cudaMemsetAsync(c.bar(), 0, (2 * sizeof(unsigned)) * n + sizeof(unsigned), c.s));
     }
     auto launch = [&]() -> cudaError_t {
       if (small) return launch_cg_cluster<T>(n, ddesc, csize, csmem, cmax, c.st(), c.s);
-      return launch_cg_persistent<T>(n, ddesc, grid_total, c.st(), c.partials(), c.bar(), c.s);
+      return launch_cg_persistent<T>(n, ddesc, grid_total, c.st(), c.partials(), c.bar(), c.wait_ns, tma, c.s);
     };
     const int kind = small ? (sizeof(T) == 8 ? EXCMG_K_CG_CLUSTER_F64 : EXCMG_K_CG_CLUSTER_F32)
                            : (sizeof(T) == 8 ? EXCMG_K_CG_F64 : EXCMG_K_CG_F32);
@@ -581,6 +636,8 @@ ResDesc make_res(const Grid3& g, int tile_z, int slot, const double* x, View f,
   r.f = f;
   r.src = src;
   r.want_b = 1;
+  r.osy = g.sy;
+  r.osz = g.sz;
   return r;
 }
 
@@ -633,6 +690,8 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     tiles += it.d64.t.count();
     if (mixed) {
       r.r = it.d32.r;
+      r.osy = it.d32.g.sy;  // the padded float32 layout
+      r.osz = it.d32.g.sz;
       // the inner solve stops at inner_tol x its starting residual, or as soon as its
       // residual is below half the outer target (more float32 steps would be wasted:
       // EXCMG's initial guess is often within a few orders of the tolerance)
@@ -703,7 +762,7 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     return EXCMG_OK;
   }
   for (auto& it : items)
-    CK(cudaMemsetAsync(it.d32.x, 0, sizeof(float) * it.nodes, c.s));
+    CK(cudaMemsetAsync(it.d32.x, 0, sizeof(float) * it.d32.g.nodes(), c.s));
   std::vector<int> cur(n);
   for (int a = 0; a < n; ++a) cur[a] = a;
   for (int pass = 0;; ++pass) {
@@ -759,6 +818,7 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
       const double nint = (double)(d.g.nx - 1) * (d.g.ny - 1) * (d.g.nz - 1);
       d.scale = (rr > 0.0 && nint > 0.0) ? 1.0 / sqrt(rr / nint) : 1.0;
       if (!isfinite(d.scale) || d.scale <= 0.0) d.scale = 1.0;
+      d.fold_scale = 1;  // applied by the CG engine (cg_loop)
       fd.push_back(d);
       fslots.push_back(d.slot);
     }
@@ -766,17 +826,35 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     const int fgrid = tiles_grid(ft);
     double fnodes = 0.0;
     for (int a : next) fnodes += (double)items[a].nodes;
+    // tensor maps of r, p_a, p_b for the float32 engine that stages planes by tensor copies
+    std::vector<TmapSet> maps(nf);
+    bool maps_ok = true;
+    for (int k = 0; k < nf && maps_ok; ++k)
+      maps_ok = encode_plane_map(&maps[k].r, fd[k].r, fd[k].g) &&
+                encode_plane_map(&maps[k].pa, fd[k].pa, fd[k].g) &&
+                encode_plane_map(&maps[k].pb, fd[k].pb, fd[k].g);
+    if (maps_ok) {
+      CK(cudaMemcpyAsync(c.tmaps(), maps.data(), sizeof(TmapSet) * nf, cudaMemcpyHostToDevice, c.s));
+      for (int k = 0; k < nf; ++k) fd[k].tm = c.tmaps() + k;
+    }
     CK(cudaMemcpyAsync(c.cgf(), fd.data(), sizeof(CGDesc<float>) * nf, cudaMemcpyHostToDevice, c.s));
-    CK(c.timed(EXCMG_K_CORRECT, fnodes, [&] { return launch_scale_rhs(nf, c.cgf(), ft, fgrid, c.st(), c.s); }));
     e = cg_loop<float>(c, nf, c.cgf(), ft, fgrid, fslots, nslots, o->chunk, hs, fnodes, fd);
     if (e != EXCMG_OK) return e;
+    std::vector<int> go;
     for (int a : next) {
-      items[a].iters += hs[items[a].d32.slot].iter;
+      const CGState& S = hs[items[a].d32.slot];
+      items[a].iters += S.iter;
       items[a].refs += 1;
-      // an inner solve that hits max_iter is not fatal: refinement continues
+      // an inner solve that hits max_iter is not fatal: refinement continues; a device
+      // wait that ran out or a non-finite reduction ends this system's refinement
+      if (S.status == EXCMG_ERR_TIMEOUT || S.status == EXCMG_ERR_NONFINITE)
+        items[a].status = S.status;
+      else
+        go.push_back(a);
     }
     CK(c.timed(EXCMG_K_CORRECT, fnodes, [&] { return launch_add_correction(nf, c.cgf(), ft, fgrid, c.s); }));
-    cur = next;
+    if (go.empty()) return EXCMG_OK;
+    cur = go;
   }
 }
 
@@ -790,6 +868,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   it.eps = (l < 2) ? o->eps_coarse : o->eps * std::pow(ratio, (double)((int)p.lv.size() - 1 - l));
   it.nodes = g.nodes();
   it.res = make_res(g, o->tile_z, slot, p.level_u(l), p.fview(l), nullptr);
+  it.res.forcing = o->rhs_norm == EXCMG_RHS_NORM_FORCING;
   CGDesc<double>& d = it.d64;
   d.g = g;
   d.A = it.res.A;
@@ -801,14 +880,16 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   d.pb = reinterpret_cast<double*>(p.base + p.L.pb);
   d.q = reinterpret_cast<double*>(p.base + p.L.q);
   d.direct = 0;  // set by the cascade for its DSOLVE levels
+  d.forcing = it.res.forcing;
   const bool res = p.L.s1 > 0 && g.nodes() <= kResidentMaxNodes;
   d.s0 = res ? reinterpret_cast<double*>(p.base + p.L.s0) : nullptr;
   d.s1 = res ? reinterpret_cast<double*>(p.base + p.L.s1) : nullptr;
   d.aux = nullptr;
   CGDesc<float>& f = it.d32;
-  f.g = g;
+  f.g = padded_f32(g);  // float32 vectors: padded rows
   f.A = it.res.A;
-  f.t = t;
+  // slabs of whole tensor copies (unless the caller fixed tile_z)
+  f.t = o->tile_z > 0 ? t : make_tiling(g, tma_slab_depth(tz));
   f.slot = slot;
   f.x = reinterpret_cast<float*>(p.base + p.L.e32);
   f.r = reinterpret_cast<float*>(p.base + p.L.r32);
@@ -818,7 +899,11 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   f.s0 = f.s1 = nullptr;
   f.direct = 0;
   f.aux = p.level_u(l);
+  f.aux_sy = g.sy;
+  f.aux_sz = g.sz;
   f.scale = 1.0;
+  f.fold_scale = 0;
+  f.tm = nullptr;
   it.rhs_cache = p.L.rhs64 ? reinterpret_cast<double*>(p.base + p.L.rhs64) : nullptr;
   return it;
 }
@@ -839,6 +924,7 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
   if (o->fixed_iters)
     for (size_t l = 0; l < P[0].lv.size(); ++l) max_count = std::max<long long>(max_count, o->fixed_iters[l]);
   c.persistent_ok = (long long)kMaxGrid * (2 * max_count + 4) < (1LL << 32);
+  c.set_waits(o);
   c.defer = o->precision == EXCMG_FP64;
   struct Report {
     excmg_stats* st;
@@ -1036,6 +1122,9 @@ void excmg_default_options(excmg_options* o) {
   o->dsolve = EXCMG_DSOLVE_DIRECT;
   o->eps_ratio = 1.0;
   o->prolong = EXCMG_PROLONG_QUARTIC;
+  o->rhs_norm = EXCMG_RHS_NORM_LIFT;
+  o->wait_timeout_ms = 0.0;
+  o->test_phantom_blocks = 0;
 }
 
 const char* excmg_status_string(excmg_status s) {
@@ -1230,6 +1319,7 @@ excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_optio
   if (opt->profile) c.prof = &prof;
   const long long max_count = opt->fixed_iters ? std::max(opt->max_iter, opt->fixed_iters[0]) : opt->max_iter;
   c.persistent_ok = (long long)kMaxGrid * (2 * max_count + 4) < (1LL << 32);
+  c.set_waits(opt);
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
   excmg_status e = solve_items(c, items, opt, 1, opt->fixed_iters);
   if (e != EXCMG_OK) return e;
@@ -1319,6 +1409,7 @@ excmg_status excmg_adjoint(const excmg_grid* grid, const double* dLdu, const exc
   p.base = c.ws + c.H.bytes + align_up(sizeof(double) * nf);
   p.L = prob_layout(p.lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt));
   c.persistent_ok = (long long)kMaxGrid * (2LL * opt->max_iter + 4) < (1LL << 32);
+  c.set_waits(opt);
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
   CK(cudaMemsetAsync(lam, 0, sizeof(double) * nf, c.s));
   Item it = make_item(p, 0, 0, opt);

@@ -7,6 +7,7 @@
 // with zero boundary is exactly A p on the interior unknowns (Section 2, eq. FD).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,6 +47,13 @@ struct Grid3 {
 };
 
 Grid3 make_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz);
+// The same grid with the row pitch of the float32 CG vectors: rows padded to a multiple
+// of 4 floats (16 bytes), so that every row and plane starts 16-byte aligned, as the
+// tensor copies (cp.async.bulk.tensor) and 16-byte vector accesses need.
+Grid3 padded_f32(const Grid3& g);
+
+// The option checks every entry point applies (excmg_api.cu).
+bool options_valid(const excmg_options* o);
 
 // Weights of A = -(printed left-hand side of eq. compact).  a = 1/hx^2 ...
 // centre 8(a+b+c); x-faces -(4a-b-c); y-faces -(4b-a-c); z-faces -(4c-a-b);
@@ -92,6 +100,13 @@ Tiling make_res_tiling(const Grid3& g, int tz);
 int choose_res_tz(const Grid3& g, int grid_blocks, int requested);
 int choose_tz(const Grid3& g, int grid_blocks, int requested);
 
+// Tensor maps of one float32 CG problem (cp.async.bulk.tensor): r and the two p buffers,
+// each a 3D map of the padded array (x extent nx + 1, so the padding reads as zero) with
+// a box of one stencil plane (kTX + 8) x (kTY + 2) x 1.
+struct alignas(64) TmapSet {
+  CUtensorMap r, pa, pb;
+};
+
 // One problem of a CG phase.
 template <typename T>
 struct CGDesc {
@@ -108,8 +123,11 @@ struct CGDesc {
   T* s0;                  // resident CG (float64 grids up to kResidentMaxNodes): s by
   T* s1;                  //   step parity (NULL elsewhere)
   double* aux;            // MIXED inner solve: the float64 level solution u += x / scale
+  long long aux_sy, aux_sz;  // node strides of aux (unpadded float64 layout)
   double scale;           // MIXED inner solve: it solves A x = scale * r (r scaled to O(1)
                           // so float32 products neither underflow nor overflow)
+  int fold_scale;         // 1: r is still unscaled; the first CG step applies `scale`
+  const TmapSet* tm;      // float32 persistent CG: tensor maps of r, pa, pb (device)
   int blk_begin;          // persistent CG: this problem's blocks are [blk_begin,
   int blk_count;          //   blk_begin + blk_count) of the cooperative grid
   int direct;             // 1: the level is solved by DSOLVE (k_dsolve), not by CG
@@ -117,6 +135,7 @@ struct CGDesc {
   View gb;
   double* hist;           // NULL, or r.r after each CG step k = 1 .. hist_len - 1 (device)
   int hist_len;
+  int forcing;            // DSOLVE: ||f_h|| of the state is the forcing norm (rhs_norm)
 };
 
 // One problem of a residual phase: r = LHS(u) - RHS(f) (= b - A u_I) in float64,
@@ -134,9 +153,14 @@ struct ResDesc {
                         // refinement steps after the first reuse -RHS(f) from rhs_out)
   double* rhs_out;      // NULL, or receives -RHS(f) on interior nodes (f path only)
   void* r;              // TR* output
+  long long osy, osz;   // node strides of r (the padded layout when TR is float; the
+                        // padding columns nx + 1 .. osy - 1 are written as zeros)
   double tol_b2;        // tol2 = max(tol_b2 * bb, tol_r2 * rr)
   double tol_r2;
   int want_b;           // compute bb (else keep the state's bb)
+  int forcing;          // bb = ||RHS(f)||^2 over the interior (the FORCING reading of
+                        // ||f_h||), or ||b||^2 with the lift where that is zero; else
+                        // bb = ||b||^2 (LIFT)
   int max_iter;
   int fixed;            // exact iteration count
   double* hist;         // NULL, or receives r.r of the start in hist[0] (device)
@@ -183,9 +207,21 @@ size_t cluster_cg_smem(const Grid3& g, int csize, size_t elem);
 template <typename T>
 cudaError_t launch_cg_cluster(int nprob, const CGDesc<T>* descs, int csize, size_t smem,
                               long long max_nodes, CGState* st, cudaStream_t s);
+// wait_ns bounds every device-side wait of the launch (grid barriers, tensor-copy
+// completions); tma selects the float32 engine whose stencil planes stream through
+// tensor copies (every problem's desc.tm set).
 template <typename T>
 cudaError_t launch_cg_persistent(int nprob, const CGDesc<T>* descs, int grid, CGState* st,
-                                 double* partials, unsigned* bar, cudaStream_t s);
+                                 double* partials, unsigned* bar, unsigned long long wait_ns,
+                                 bool tma, cudaStream_t s);
+// Co-resident blocks of the float32 tensor-copy engine.
+int persistent_cg_blocks_tma();
+// Slab depth for the float32 tensor-copy engine: tz moved to the nearest depth whose
+// tz + 2 planes (the slab and its two halo planes) are whole copies.
+int tma_slab_depth(int tz);
+// Encodes the tensor map of one padded float32 node array of grid g32 (padded_f32);
+// false if the driver entry point is missing or the encoding fails.
+bool encode_plane_map(CUtensorMap* m, float* base, const Grid3& g32);
 
 // All CG steps of ONE float64 grid of up to kResidentMaxNodes nodes in a cooperative
 // grid whose blocks keep the level's vectors in shared memory (resident_cg.cu).

@@ -95,9 +95,10 @@ extern "C" excmg_status excmg_cg_noalloc(const excmg_grid* grid, const double* f
   if (!grid || !f || !u || !opt || u == f) return EXCMG_ERR_INVALID_ARG;
   if (!(grid->Lx > 0) || !(grid->Ly > 0) || !(grid->Lz > 0)) return EXCMG_ERR_INVALID_ARG;
   if (grid->Nx < 2 || grid->Ny < 2 || grid->Nz < 2) return EXCMG_ERR_INVALID_ARG;
-  if (opt->precision != EXCMG_FP64 || !(opt->eps >= 0) || opt->max_iter < 0 || opt->chunk < 0 ||
-      opt->tile_z < 0 || opt->tile_z > 256)
-    return EXCMG_ERR_INVALID_ARG;
+  if (!options_valid(opt) || opt->precision != EXCMG_FP64) return EXCMG_ERR_INVALID_ARG;
+  // the residual history and the per-launch timing need host-side buffers and events
+  // this entry point does not keep: refused rather than silently left unfilled
+  if (opt->history || opt->profile) return EXCMG_ERR_INVALID_ARG;
   if (opt->fixed_iters && opt->fixed_iters[0] < 0) return EXCMG_ERR_INVALID_ARG;
   const long long nodes = (long long)(grid->Nx + 1) * (grid->Ny + 1) * (grid->Nz + 1);
   if (nodes > (1LL << 40)) return EXCMG_ERR_INVALID_ARG;
@@ -126,6 +127,7 @@ extern "C" excmg_status excmg_cg_noalloc(const excmg_grid* grid, const double* f
   rd.src = nullptr;
   rd.r = base + L.r;
   rd.want_b = 1;
+  rd.forcing = opt->rhs_norm == EXCMG_RHS_NORM_FORCING;
   rd.fixed = opt->fixed_iters ? 1 : 0;
   rd.max_iter = opt->fixed_iters ? opt->fixed_iters[0] : opt->max_iter;
   rd.tol_b2 = opt->eps * opt->eps;

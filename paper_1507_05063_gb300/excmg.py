@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("chunk", ctypes.c_int), ("mixed_min_nodes", ctypes.c_longlong),
                 ("profile", ctypes.c_int), ("dsolve", ctypes.c_int), ("eps_ratio", ctypes.c_double),
                 ("prolong", ctypes.c_int), ("history", ctypes.POINTER(ctypes.c_double)),
-                ("history_len", ctypes.c_int)]
+                ("history_len", ctypes.c_int), ("rhs_norm", ctypes.c_int),
+                ("wait_timeout_ms", ctypes.c_double), ("test_phantom_blocks", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -136,11 +137,13 @@ def make_grid(L, N, N0=(2, 2, 2)):
 
 DSOLVE = {"direct": 0, "cg": 1}
 PROLONG = {"quartic": 0, "quadratic": 1, "linear": 2}
+RHS_NORM = {"lift": 0, "forcing": 1}
 
 
 def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
                  inner_tol=1e-4, max_refine=50, fixed_iters=None, tile_z=0, chunk=0, profile=0,
-                 mixed_min_nodes=0, dsolve="direct", eps_ratio=1.0, prolong="quartic", history=0):
+                 mixed_min_nodes=0, dsolve="direct", eps_ratio=1.0, prolong="quartic", history=0,
+                 rhs_norm="lift", wait_timeout_ms=0.0, test_phantom_blocks=0):
     o = Options()
     excmg_default_options(ctypes.byref(o))
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else int(precision)
@@ -156,6 +159,9 @@ def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
     o.dsolve = DSOLVE[dsolve] if isinstance(dsolve, str) else int(dsolve)
     o.eps_ratio = float(eps_ratio)
     o.prolong = PROLONG[prolong] if isinstance(prolong, str) else int(prolong)
+    o.rhs_norm = RHS_NORM[rhs_norm] if isinstance(rhs_norm, str) else int(rhs_norm)
+    o.wait_timeout_ms = float(wait_timeout_ms)
+    o.test_phantom_blocks = int(test_phantom_blocks)
     keep = {}
     if fixed_iters is not None:
         keep["fixed"] = (ctypes.c_int * len(fixed_iters))(*[int(v) for v in fixed_iters])
@@ -273,7 +279,7 @@ def exp_true(uh, u2h, L, stream=None):
     return ut
 
 
-def cg(f, u, L, stream=None, ws=None, allow_not_converged=False, **opts):
+def cg(f, u, L, stream=None, ws=None, allow_not_converged=False, allow_timeout=False, **opts):
     """CG on one grid from u's interior (u's boundary = g), in place.  Returns stats."""
     N = (f.shape[2] - 1, f.shape[1] - 1, f.shape[0] - 1)
     grid = make_grid(L, N)
@@ -287,7 +293,7 @@ def cg(f, u, L, stream=None, ws=None, allow_not_converged=False, **opts):
     status = excmg_cg(ctypes.byref(grid), _node_array(f, N, "f"), ctypes.byref(o),
                       _node_array(u, N, "u"), _ptr(ws), ws.numel(), ctypes.byref(st),
                       _stream(stream))
-    _check(status, "excmg_cg", allow=(2,) if allow_not_converged else ())
+    _check(status, "excmg_cg", allow=((2,) if allow_not_converged else ()) + ((5,) if allow_timeout else ()))
     d = st.to_dict()
     d["status"] = STATUS[status]
     if "history" in _keep:

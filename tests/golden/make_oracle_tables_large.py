@@ -1,10 +1,15 @@
-"""Writes oracle_tables_large.txt: the FP64 oracle's EXCMG errors and per-level CG step
-counts on the meshes of paper_tables_gpu.txt (64^3 ... 256^3; Example 4: 128x64x32 ...
-512x256x128), at each example's tolerance and coarsest grid (Section 5), DSOLVE dense.
+"""Writes oracle_tables_large.txt (the "lift" reading of ||f_h|| in the stopping test of
+Algorithm 1) and oracle_tables_large_forcing.txt (the "forcing" reading): the FP64
+oracle's EXCMG errors and per-level CG step counts on the meshes of paper_tables_gpu.txt
+(64^3 ... 256^3; Example 4: 128x64x32 ... 512x256x128), at each example's tolerance and
+coarsest grid (Section 5), DSOLVE dense.
 
-Calls only the oracle and the closed-form inputs; a few minutes on one CPU core.
-Usage: python tests/golden/make_oracle_tables_large.py
+Calls only the oracle and the closed-form inputs; the runs are independent and go to a
+pool of worker processes (lift: a few minutes; forcing: tens of minutes, its finest
+grids take many more CG steps).
+Usage: python tests/golden/make_oracle_tables_large.py [lift|forcing] [workers]
 """
+import multiprocessing
 import os
 import sys
 
@@ -21,11 +26,15 @@ MESHES = {ex: [(n, n, n) for n in (64, 128, 256)] for ex in SETUP}
 MESHES["ex4"] = [(128, 64, 32), (256, 128, 64), (512, 256, 128)]
 
 
-def errors(name, N):
+OUT = {"lift": "oracle_tables_large.txt", "forcing": "oracle_tables_large_forcing.txt"}
+
+
+def errors(name, N, reading="lift"):
     eps, N0 = SETUP[name]
     prob = P.PROBLEMS[name]
     f, g, u = P.make_inputs(prob, N)
-    res = O.excmg(f, g, (1.0, 1.0, 1.0), N, N0, eps=eps, eps_coarse=eps, dsolve="dense")
+    res = O.excmg(f, g, (1.0, 1.0, 1.0), N, N0, eps=eps, eps_coarse=eps, dsolve="dense",
+                  rhs_norm=reading)
     uh, ut, w = res["u"][-1], res["ut"][-1], res["w"][-1]
     gx, gy, gz = O.gradient(uh, res["h"][-1])
     ex, ey, ez = P.exact_gradient(prob, N)
@@ -39,19 +48,31 @@ def errors(name, N):
     return vals, res["iters"]
 
 
+def _run(job):
+    name, N, reading = job
+    vals, iters = errors(name, N, reading)
+    mesh = "x".join(str(n) for n in N)
+    out = [f"{name} {mesh} {norm} {qty} {v:.6e}" for (norm, qty), v in vals.items()]
+    out.append(f"{name} {mesh} iters {','.join(str(i) for i in iters)}")
+    print(out[-1], flush=True)
+    return out
+
+
 def main():
-    lines = ["# FP64 oracle (oracle/excmg_oracle.py, DSOLVE dense) on the meshes of",
-             "# paper_tables_gpu.txt; written by make_oracle_tables_large.py.",
+    reading = sys.argv[1] if len(sys.argv) > 1 else "lift"
+    workers = int(sys.argv[2]) if len(sys.argv) > 2 else 1
+    lines = [f"# FP64 oracle (oracle/excmg_oracle.py, DSOLVE dense, ||f_h|| reading '{reading}')",
+             "# on the meshes of paper_tables_gpu.txt; written by make_oracle_tables_large.py.",
              "# Rows: example mesh norm quantity value  |  example mesh iters c0,c1,... (per level)"]
-    for name in sorted(SETUP):
-        for N in MESHES[name]:
-            vals, iters = errors(name, N)
-            mesh = "x".join(str(n) for n in N)
-            for (norm, qty), v in vals.items():
-                lines.append(f"{name} {mesh} {norm} {qty} {v:.6e}")
-            lines.append(f"{name} {mesh} iters {','.join(str(i) for i in iters)}")
-            print(lines[-1], flush=True)
-    with open(os.path.join(HERE, "oracle_tables_large.txt"), "w") as fh:
+    jobs = [(name, N, reading) for name in sorted(SETUP) for N in MESHES[name]]
+    if workers > 1:
+        with multiprocessing.get_context("spawn").Pool(workers) as pool:
+            results = pool.map(_run, jobs, chunksize=1)
+    else:
+        results = [_run(j) for j in jobs]
+    for r in results:
+        lines.extend(r)
+    with open(os.path.join(HERE, OUT[reading]), "w") as fh:
         fh.write("\n".join(lines) + "\n")
 
 

@@ -42,6 +42,43 @@ def test_512x256x128_fp64_full_cascade(X):
     assert np.max(np.abs(ut - ref["ut"][-1])) <= 1e-10 * np.max(np.abs(uo))
 
 
+def test_512x256x128_fp64_cg_steps_persistent_engine(X):
+    """Five float64 CG steps on the full 512x256x128 grid from EXP_finite's start -- the
+    cooperative persistent engine with its flat vectorised update (nodes >= blocks x
+    chunk) -- against the oracle's CG with the same five steps: rel L-inf <= 1e-10."""
+    N, N0, L = (512, 256, 128), (8, 4, 2), (1.0, 1.0, 1.0)
+    f, g, _ = P.make_inputs(P.PROBLEMS["exp3"], N)
+    rng = np.random.default_rng(21)
+    u0 = g.copy()
+    u0[1:-1, 1:-1, 1:-1] += 1e-6 * rng.standard_normal((N[2] - 1, N[1] - 1, N[0] - 1))
+    want, it, _ = O.cg(u0, f, O.meshsizes(L, N), 0.0, fixed_iters=5)
+    u = torch.from_numpy(u0).cuda()
+    st = X.cg(torch.from_numpy(f).cuda(), u, L, eps=0.0, fixed_iters=[5], profile=1)
+    assert st["iters"][0] == 5
+    assert "cg_f64" in st["profile"]  # the persistent engine ran the steps
+    got = u.cpu().numpy()
+    assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want))
+
+
+def test_512x256x128_mixed_refines_within_fp64_error(X):
+    """MIXED on the full 512x256x128 workload with float32 inner solves on every level
+    (mixed_min_nodes = 1) and a tolerance tight enough that every level, the finest
+    included, needs refinement steps and the algebraic error falls below the
+    discretisation error: every level meets eps in the float64 residual, and the error
+    against the exact solution is within 1.05x of the FP64 oracle's at that tolerance."""
+    N, N0, L, eps = (512, 256, 128), (8, 4, 2), (1.0, 1.0, 1.0), 1e-13
+    f, g, u = P.make_inputs(P.PROBLEMS["exp3"], N)
+    res = X.solve(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), L, N0, eps=eps,
+                  eps_coarse=1e-12, precision="mixed", mixed_min_nodes=1)
+    st = res["stats"]
+    assert sum(st["refinements"][2:]) >= 3 and st["refinements"][-1] >= 1, st["refinements"]
+    assert all(r <= eps * 1.0000001 for r in st["relres"][2:])
+    ref = O.excmg(f, g, L, N, N0, eps=eps, eps_coarse=1e-12, dsolve="dense", want_utilde=False)
+    e_or = np.max(np.abs(ref["u"][-1] - u))
+    e_mx = np.max(np.abs(res["u"].cpu().numpy() - u))
+    assert e_mx <= 1.05 * e_or, (e_mx, e_or)
+
+
 def _windows(rng, N, k, halo):
     """k random window origins (x, y, z) leaving `halo` nodes of room on each side."""
     return [tuple(int(rng.integers(halo, N[d] - halo)) for d in range(3)) for _ in range(k)]

@@ -82,3 +82,14 @@ def test_noalloc_refuses_grids_beyond_its_scratch(X):
     status = X.excmg_cg_noalloc(ctypes.byref(grid), fake, ctypes.byref(o), ctypes.c_void_p(2 << 20),
                                 None, None)
     assert status == 6  # EXCMG_ERR_WORKSPACE, before any work is enqueued
+
+
+def test_noalloc_refuses_options_it_cannot_honour(X):
+    """The residual history and the per-launch timing need host buffers and events that
+    the allocation-free entry point does not keep: it refuses them (EXCMG_ERR_INVALID_ARG)
+    instead of leaving them unfilled; so are invalid options excmg_cg would refuse."""
+    N, L = (16, 16, 16), (1.0, 1.0, 1.0)
+    fd, u0 = _start(P.PROBLEMS["ex1"], N, L, seed=3)
+    for opts in (dict(history=8), dict(profile=1), dict(eps_ratio=-1.0), dict(precision="mixed")):
+        status, _ = _noalloc(X, fd, u0.clone(), L, **opts)
+        assert status == 1, opts
