@@ -391,9 +391,21 @@ __device__ __forceinline__ double update_flat(const CGDesc<T>& d, int bl, int G,
   double acc = 0.0;
   constexpr int V = Vec<T>::n;
   using VT = typename Vec<T>::type;
-  const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
-                     reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(pn)) & 15) == 0;
-  for (long long c0 = (long long)bl * kChunk; c0 < n; c0 += (long long)G * kChunk) {
+  // 16-byte vectors when the four arrays sit equally far from a 16-byte boundary: the
+  // `lead` elements before it are done one by one (block 0), the rest in vectors
+  const uintptr_t ax = reinterpret_cast<uintptr_t>(x);
+  const bool vec = (((ax ^ reinterpret_cast<uintptr_t>(r)) | (ax ^ reinterpret_cast<uintptr_t>(q)) |
+                     (ax ^ reinterpret_cast<uintptr_t>(pn))) & 15) == 0 && (ax % sizeof(T)) == 0;
+  const long long lead = vec ? (long long)(((16 - (ax & 15)) & 15) / sizeof(T)) : 0;
+  if (bl == 0 && threadIdx.x < lead && threadIdx.x < n) {
+    const long long o = threadIdx.x;
+    const T xv = fmaT(alpha, ldv(pn + o), ldv(x + o));
+    const T rv = fmaT(-alpha, ldv(q + o), sigma * ldv(r + o));
+    x[o] = xv;
+    r[o] = rv;
+    acc += (double)(rv * rv);
+  }
+  for (long long c0 = lead + (long long)bl * kChunk; c0 < n; c0 += (long long)G * kChunk) {
     const long long c1 = c0 + kChunk < n ? c0 + kChunk : n;
     T tacc = T(0);
     if (vec && c1 - c0 == kChunk) {
@@ -444,14 +456,19 @@ __device__ __forceinline__ double update_flat(const CGDesc<T>& d, int bl, int G,
 // apart by up to kStages planes and hide each other's latencies.  Out-of-range boxes
 // (x < 0, y < 0, planes -1 and nz + 1, the padding columns) read as zeros.
 // ---------------------------------------------------------------------------------
-constexpr int kBoxX = kTX + 8;
-constexpr int kBoxY = kTY + 2;
+#ifndef EXCMG_TMA_ROWS
+#define EXCMG_TMA_ROWS 1
+#endif
 #ifndef EXCMG_TMA_STAGES
-#define EXCMG_TMA_STAGES 4
+#define EXCMG_TMA_STAGES 3
 #endif
 #ifndef EXCMG_TMA_PLANES
-#define EXCMG_TMA_PLANES 4
+#define EXCMG_TMA_PLANES 6
 #endif
+constexpr int kRT = EXCMG_TMA_ROWS;        // y-rows per thread (consecutive)
+constexpr int kTileY = kTY * kRT;          // y-rows of a tile of this engine
+constexpr int kBoxX = kTX + 8;
+constexpr int kBoxY = kTileY + 2;
 constexpr int kStages = EXCMG_TMA_STAGES;
 constexpr int kZs = EXCMG_TMA_PLANES;  // planes per copy (the box's z extent)
 constexpr unsigned kBoxBytes = kBoxX * kBoxY * kZs * sizeof(float);
@@ -531,11 +548,27 @@ struct RingPhases {
   unsigned full = 0, empty = 0;
 };
 
-// The K1 body over the tiles bl, bl + G, ... of one float32 problem with tensor-copy
-// staging: p_new = sigma r + beta p_old (sigma = the folded RHS scale on the first step,
-// else 1; p_old not read on the first step), q = A p_new, and this thread's share of
-// p.q.  A tile's planes z0 - 1 .. z1 arrive kZs at a time (the last box of a tile may
-// reach past z1; those planes are not used).  A wait that runs out sets ring.abort;
+// Origin of tile lt of the tensor-copy engine's tiling (tiles of kTX x kTileY columns).
+__device__ __forceinline__ TileXYZ tma_tile_coords(const Grid3& g, const Tiling& tl, long long lt) {
+  TileXYZ c;
+  const int bx = (int)(lt % tl.ntx);
+  const long long r = lt / tl.ntx;
+  const int by = (int)(r % tl.nty);
+  const int bz = (int)(r / tl.nty);
+  c.x0 = bx * kTX;
+  c.y0 = by * kTileY;
+  c.z0 = bz * tl.tz;
+  c.z1 = min(c.z0 + tl.tz, g.nz + 1);
+  return c;
+}
+
+// The K1 body over the tiles bl, bl + G, ... (desc.tt: tiles of kTX x kTileY columns) of
+// one float32 problem with tensor-copy staging: p_new = sigma r + beta p_old (sigma = the
+// folded RHS scale on the first step, else 1; p_old not read on the first step),
+// q = A p_new, and this thread's share of p.q.  Each thread applies the stencil to kRT
+// consecutive rows of one column, so the rows share the p_new values they have in
+// common.  A tile's planes z0 - 1 .. z1 arrive kZs at a time (the last box of a tile
+// may reach past z1; those planes are not used).  A wait that runs out sets ring.abort;
 // every thread leaves its loop when it sees it, and the flag is read again after the
 // block barrier that follows the call.
 __device__ double spmv_tiles_tma(const CGDesc<float>& d, int bl, int G, bool first, float beta,
@@ -543,7 +576,7 @@ __device__ double spmv_tiles_tma(const CGDesc<float>& d, int bl, int G, bool fir
                                  float* __restrict__ pnew, TmaRing& R, RingPhases& ph,
                                  unsigned long long wait_ns) {
   const Grid3 g = d.g;
-  const Tiling tl = d.t;
+  const Tiling tl = d.tt;
   const long long T = tl.count();
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX, lane = threadIdx.x & 31;
   float* __restrict__ q = d.q;
@@ -557,7 +590,7 @@ __device__ double spmv_tiles_tma(const CGDesc<float>& d, int bl, int G, bool fir
   TileXYZ lc{0, 0, 0, 0};
   int lkk = 0;
   if (lt < T) {
-    lc = tile_coords(g, tl, lt);
+    lc = tma_tile_coords(g, tl, lt);
     lkk = lc.z0 - 1;
   }
   int issued = 0, consumed = 0;  // boxes copied / applied in this call (thread 0's counts)
@@ -570,7 +603,7 @@ __device__ double spmv_tiles_tma(const CGDesc<float>& d, int bl, int G, bool fir
     if (lkk > lc.z1) {
       lt += G;
       if (lt < T) {
-        lc = tile_coords(g, tl, lt);
+        lc = tma_tile_coords(g, tl, lt);
         lkk = lc.z0 - 1;
       }
     }
@@ -580,15 +613,18 @@ __device__ double spmv_tiles_tma(const CGDesc<float>& d, int bl, int G, bool fir
   int slot = 0;
   double acc = 0.0;
   bool stop = false;
-  // this thread's 3x3 neighbourhood in a plane of a stage: rows ty .. ty + 2, columns
-  // tx + 3 .. tx + 5 (stage column c holds x = x0 - 4 + c)
-  const int base = ty * kBoxX + tx + 3;
+  // this thread's neighbourhood in a plane of a stage: rows ty kRT .. ty kRT + kRT + 1,
+  // columns tx + 3 .. tx + 5 (stage column c holds x = x0 - 4 + c, row r y = y0 - 1 + r)
+  const int base = ty * kRT * kBoxX + tx + 3;
   for (long long t = bl; t < T && !stop; t += G) {
-    const TileXYZ c = tile_coords(g, tl, t);
-    const int i = c.x0 + tx, j = c.y0 + ty;
-    const bool own = (i < g.sy) && (j <= g.ny);
-    const bool inxy = (i > 0) && (i < g.nx) && (j > 0) && (j < g.ny);
-    float Pm1 = 0.f, Cm1 = 0.f, Tm1 = 0.f, Tm2 = 0.f, tacc = 0.f;
+    const TileXYZ c = tma_tile_coords(g, tl, t);
+    const int i = c.x0 + tx, j0 = c.y0 + ty * kRT;
+    // own nodes include the padding columns nx + 1 .. sy - 1, which get p = q = 0
+    const bool colx = (i > 0) && (i < g.nx), ownx = i < g.sy;
+    float Pm1[kRT], Cm1[kRT], Tm1[kRT], Tm2[kRT];
+#pragma unroll
+    for (int r = 0; r < kRT; ++r) Pm1[r] = Cm1[r] = Tm1[r] = Tm2[r] = 0.f;
+    float tacc = 0.f;
     for (int k0 = c.z0 - 1; k0 <= c.z1; k0 += kZs) {
       if (!mbar_wait(&R.full[slot], (ph.full >> slot) & 1u, wait_ns)) *abort = 1;
       ph.full ^= 1u << slot;
@@ -598,35 +634,39 @@ __device__ double spmv_tiles_tma(const CGDesc<float>& d, int bl, int G, bool fir
       }
       const int np = min(kZs, c.z1 + 1 - k0);  // planes of this box that the tile uses
 #pragma unroll 1
-      for (int pz = 0; pz < kZs; ++pz) {
-        if (pz < np) {
-          const float* rs = &R.stage[slot][0][pz * kBoxY * kBoxX + base];
-          const float* ps = &R.stage[slot][1][pz * kBoxY * kBoxX + base];
-          float v[3][3];
+      for (int pz = 0; pz < np; ++pz) {
+        const float* rs = &R.stage[slot][0][pz * kBoxY * kBoxX + base];
+        const float* ps = &R.stage[slot][1][pz * kBoxY * kBoxX + base];
+        float v[kRT + 2][3];
 #pragma unroll
-          for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < kRT + 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b)
-              v[a][b] = first ? sigma * rs[a * kBoxX + b] : fmaf(beta, ps[a * kBoxX + b], rs[a * kBoxX + b]);
-          const float P = v[1][1];
-          const float SX = v[1][0] + v[1][2];
-          const float SY = v[0][1] + v[2][1];
-          const float EXY = (v[0][0] + v[0][2]) + (v[2][0] + v[2][2]);
+          for (int b = 0; b < 3; ++b)
+            v[a][b] = first ? sigma * rs[a * kBoxX + b] : fmaf(beta, ps[a * kBoxX + b], rs[a * kBoxX + b]);
+        const int kc = k0 + pz - 1;
+        const bool emit = kc >= c.z0 && ownx;
+        const bool zin = kc > 0 && kc < g.nz;
+#pragma unroll
+        for (int r = 0; r < kRT; ++r) {
+          const float P = v[r + 1][1];
+          const float SX = v[r + 1][0] + v[r + 1][2];
+          const float SY = v[r][1] + v[r + 2][1];
+          const float EXY = (v[r][0] + v[r][2]) + (v[r + 2][0] + v[r + 2][2]);
           const float Ck = fmaf(c0, P, fmaf(fx, SX, fmaf(fy, SY, exy * EXY)));
           const float Tk = fmaf(fz, P, fmaf(exz, SX, eyz * SY));
-          const int kc = k0 + pz - 1;
-          if (kc >= c.z0 && own) {
+          const int j = j0 + r;
+          if (emit && j <= g.ny) {
             const long long o = i + j * g.sy + (long long)kc * g.sz;
-            const bool interior = inxy && kc > 0 && kc < g.nz;
-            const float qv = interior ? (Cm1 + Tm2) + Tk : 0.f;
-            pnew[o] = Pm1;
+            const bool interior = colx && j > 0 && j < g.ny && zin;
+            const float qv = interior ? (Cm1[r] + Tm2[r]) + Tk : 0.f;
+            pnew[o] = Pm1[r];
             q[o] = qv;
-            tacc = fmaf(Pm1, qv, tacc);
+            tacc = fmaf(Pm1[r], qv, tacc);
           }
-          Tm2 = Tm1;
-          Tm1 = Tk;
-          Cm1 = Ck;
-          Pm1 = P;
+          Tm2[r] = Tm1[r];
+          Tm1[r] = Tk;
+          Cm1[r] = Ck;
+          Pm1[r] = P;
         }
       }
       // the stage is read: this warp releases it
@@ -1365,6 +1405,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+Tiling make_tma_tiling(const Grid3& g, int tz) {
+  Tiling t;
+  t.tz = tz;
+  t.ntx = (g.nx + 1 + kTX - 1) / kTX;
+  t.nty = (g.ny + 1 + kTileY - 1) / kTileY;
+  t.ntz = (g.nz + 1 + tz - 1) / tz;
+  return t;
+}
 
 int tma_slab_depth(int tz) {
   // the slab depth nearest tz whose tz + 2 planes are whole copies of kZs planes

@@ -229,16 +229,17 @@ ProbLayout prob_layout(const std::vector<Level>& lv, bool mixed, bool need_fp64_
     }
   }
   if (mixed) {
+    const size_t v32 = sizeof(float) * nf32;
     L.r32 = off;
-    off = align_up(off + sizeof(float) * nf32);
+    off = align_up(off + v32);
     L.pa32 = off;
-    off = align_up(off + sizeof(float) * nf32);
+    off = align_up(off + v32);
     L.pb32 = off;
-    off = align_up(off + sizeof(float) * nf32);
+    off = align_up(off + v32);
     L.q32 = off;
-    off = align_up(off + sizeof(float) * nf32);
+    off = align_up(off + v32);
     L.e32 = off;
-    off = align_up(off + sizeof(float) * nf32);
+    off = align_up(off + v32);
     L.rhs64 = off;
     off = align_up(off + sizeof(double) * nf);
   }
@@ -888,8 +889,9 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   CGDesc<float>& f = it.d32;
   f.g = padded_f32(g);  // float32 vectors: padded rows
   f.A = it.res.A;
-  // slabs of whole tensor copies (unless the caller fixed tile_z)
-  f.t = o->tile_z > 0 ? t : make_tiling(g, tma_slab_depth(tz));
+  f.t = t;
+  // the tensor-copy engine: slabs of whole tensor copies (unless the caller fixed tile_z)
+  f.tt = make_tma_tiling(g, o->tile_z > 0 ? tz : tma_slab_depth(tz));
   f.slot = slot;
   f.x = reinterpret_cast<float*>(p.base + p.L.e32);
   f.r = reinterpret_cast<float*>(p.base + p.L.r32);

@@ -52,6 +52,7 @@ Grid3 make_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz);
 // tensor copies (cp.async.bulk.tensor) and 16-byte vector accesses need.
 Grid3 padded_f32(const Grid3& g);
 
+
 // The option checks every entry point applies (excmg_api.cu).
 bool options_valid(const excmg_options* o);
 
@@ -113,6 +114,7 @@ struct CGDesc {
   Grid3 g;
   Coef A;
   Tiling t;
+  Tiling tt;              // float32 tensor-copy engine: its own tiles (make_tma_tiling)
   long long tile_begin;   // first global tile index of this problem
   int slot;               // index of this problem's CGState
   T* x;
@@ -219,6 +221,9 @@ int persistent_cg_blocks_tma();
 // Slab depth for the float32 tensor-copy engine: tz moved to the nearest depth whose
 // tz + 2 planes (the slab and its two halo planes) are whole copies.
 int tma_slab_depth(int tz);
+// The tensor-copy engine's tiling of g: tiles of kTX columns x (its rows per thread x
+// kTY) rows x tz planes.
+Tiling make_tma_tiling(const Grid3& g, int tz);
 // Encodes the tensor map of one padded float32 node array of grid g32 (padded_f32);
 // false if the driver entry point is missing or the encoding fails.
 bool encode_plane_map(CUtensorMap* m, float* base, const Grid3& g32);
