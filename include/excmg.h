@@ -134,7 +134,29 @@ typedef struct {
                               complete and its wait must run out (with a short
                               wait_timeout_ms, to check that the call returns
                               EXCMG_ERR_TIMEOUT and the context stays usable) */
+  int autotune;            /* launch-shape tuning: 1 = before a single solve, time candidate
+                              slab depths of every level's residual and tiled CG engine that
+                              the cache (per level grid, engine class and device, kept for
+                              the process) lacks, and keep the fastest; 0 (default) = use the
+                              cache where it holds the level, the models elsewhere; -1 = the
+                              models only.  options.tile_z > 0 overrides both */
 } excmg_options;
+
+/* One entry of the launch-shape cache (options.autotune): a level grid and engine class
+   with the tuned and the modelled slab depths and their measured times. */
+typedef struct {
+  int N[3];                     /* the level's cells */
+  int f32;                      /* 1: its CG is the float32 engine of MIXED inner solves */
+  int res_tz, res_tz_model;     /* residual slab depth: tuned, modelled */
+  double res_ms, res_ms_model;  /* one residual launch at each (ms) */
+  int cg_tz, cg_tz_model;       /* slab depth of its CG engine (0: the engine is not tiled) */
+  double cg_ms, cg_ms_model;    /* one CG step at each (ms) */
+} excmg_tuning;
+
+/* Copies up to `max` cache entries to out (NULL: none) and returns how many there are. */
+int excmg_tuning_entries(excmg_tuning* out, int max);
+/* Empties the launch-shape cache. */
+void excmg_tuning_clear(void);
 
 /* ||f_h||_2 in the WHILE test ||A_h u_h - f_h|| > eps ||f_h|| of Algorithm 1.  The paper
    defines f_h (Section 2, after eq. FD) as the right-hand side vector of eq. (compact),
@@ -195,7 +217,7 @@ typedef struct {
    inner_tol 1e-4, max_refine 50, fixed_iters NULL, tile_z 0, chunk 0,
    mixed_min_nodes 0, profile 0, dsolve DIRECT, eps_ratio 1 (uniform tolerance),
    prolong QUARTIC, history NULL, history_len 0, rhs_norm LIFT, wait_timeout_ms 0
-   (20 s), test_phantom_blocks 0. */
+   (20 s), test_phantom_blocks 0, autotune 0. */
 void excmg_default_options(excmg_options* opt);
 
 /* Human-readable name of a status code (static string). */

@@ -6,6 +6,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "excmg_internal.cuh"
@@ -168,6 +170,7 @@ bool options_ok(const excmg_options* o) {
   if (!(o->wait_timeout_ms >= 0) || !std::isfinite(o->wait_timeout_ms) || o->wait_timeout_ms > 3.6e6)
     return false;
   if (o->test_phantom_blocks < 0 || o->test_phantom_blocks > 64) return false;
+  if (o->autotune < -1 || o->autotune > 1) return false;
   return true;
 }
 
@@ -176,6 +179,43 @@ bool options_ok(const excmg_options* o) {
 bool excmg::options_valid(const excmg_options* o) { return options_ok(o); }
 
 namespace {
+
+// ---- launch-shape tuning (options.autotune) ----
+// A process-wide cache of measured launch shapes per level grid, engine class (float64
+// CG or the float32 tensor-copy engine of MIXED inner solves) and device: the residual's
+// slab depth and the slab depth of the CG engine that runs the level.  Filled by the
+// tuning pass of excmg_solve (autotune = 1), read by every solve (autotune >= 0).
+struct TuneKey {
+  int nx, ny, nz, f32, dev;
+  bool operator<(const TuneKey& o) const {
+    if (nx != o.nx) return nx < o.nx;
+    if (ny != o.ny) return ny < o.ny;
+    if (nz != o.nz) return nz < o.nz;
+    if (f32 != o.f32) return f32 < o.f32;
+    return dev < o.dev;
+  }
+};
+std::map<TuneKey, excmg_tuning> g_tune;
+std::mutex g_tune_mu;
+
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+bool tune_lookup(const Grid3& g, bool f32, excmg_tuning* out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(TuneKey{g.nx, g.ny, g.nz, f32 ? 1 : 0, current_device()});
+  if (it == g_tune.end()) return false;
+  if (out) *out = it->second;
+  return true;
+}
+
+void tune_store(const Grid3& g, bool f32, const excmg_tuning& t) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[TuneKey{g.nx, g.ny, g.nz, f32 ? 1 : 0, current_device()}] = t;
+}
 
 // Per-problem workspace layout.
 struct ProbLayout {
@@ -859,16 +899,45 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
   }
 }
 
+// The engine class of level grid g under options o: true when its CG runs in float32
+// (MIXED inner solves; DSOLVE levels are float64).
+bool level_f32(const Grid3& g, int l, const excmg_options* o) {
+  return o->precision == EXCMG_MIXED && g.nodes() >= mixed_min(o) && l >= 2;
+}
+
+// Launch shapes of a level: the caller's tile_z, else the tuned ones (options.autotune
+// >= 0 and a cache entry), else the models.
+struct Shapes {
+  int res_tz, cg_tz, tma_tz;
+};
+Shapes level_shapes(const Grid3& g, int l, const excmg_options* o) {
+  Shapes sh;
+  const int tz = choose_tz(g, persistent_grid(1LL << 40), o->tile_z);
+  sh.cg_tz = tz;
+  sh.tma_tz = o->tile_z > 0 ? tz : tma_slab_depth(tz);
+  sh.res_tz = choose_res_tz(g, residual_grid(1LL << 40), o->tile_z);
+  excmg_tuning t;
+  if (o->tile_z == 0 && o->autotune >= 0 && tune_lookup(g, level_f32(g, l, o), &t)) {
+    sh.res_tz = t.res_tz;
+    if (level_f32(g, l, o))
+      sh.tma_tz = t.cg_tz;
+    else
+      sh.cg_tz = t.cg_tz;
+  }
+  return sh;
+}
+
 Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   const Grid3 g = p.grid(l);
-  const int tz = choose_tz(g, persistent_grid(1LL << 40), o->tile_z);
+  const Shapes sh = level_shapes(g, l, o);
+  const int tz = sh.cg_tz;
   const Tiling t = make_tiling(g, tz);
   Item it;
   memset(&it, 0, sizeof(it));
   const double ratio = o->eps_ratio > 0 ? o->eps_ratio : 1.0;
   it.eps = (l < 2) ? o->eps_coarse : o->eps * std::pow(ratio, (double)((int)p.lv.size() - 1 - l));
   it.nodes = g.nodes();
-  it.res = make_res(g, o->tile_z, slot, p.level_u(l), p.fview(l), nullptr);
+  it.res = make_res(g, sh.res_tz, slot, p.level_u(l), p.fview(l), nullptr);
   it.res.forcing = o->rhs_norm == EXCMG_RHS_NORM_FORCING;
   CGDesc<double>& d = it.d64;
   d.g = g;
@@ -891,7 +960,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   f.A = it.res.A;
   f.t = t;
   // the tensor-copy engine: slabs of whole tensor copies (unless the caller fixed tile_z)
-  f.tt = make_tma_tiling(g, o->tile_z > 0 ? tz : tma_slab_depth(tz));
+  f.tt = make_tma_tiling(g, sh.tma_tz);
   f.slot = slot;
   f.x = reinterpret_cast<float*>(p.base + p.L.e32);
   f.r = reinterpret_cast<float*>(p.base + p.L.r32);
@@ -908,6 +977,102 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   f.tm = nullptr;
   it.rhs_cache = p.L.rhs64 ? reinterpret_cast<double*>(p.base + p.L.rhs64) : nullptr;
   return it;
+}
+
+// The tuning pass of options.autotune = 1 (single solves): for every level from 2 up
+// without a cache entry, time the residual at candidate slab depths and, where the
+// level's CG engine is tiled (the persistent float64 engine above kResidentMaxNodes
+// nodes, or the float32 tensor-copy engine), three CG steps at candidate slab depths;
+// each candidate runs on the level's own solution array (overwritten by the solve
+// afterwards: boundary = g, interior = 0 at every start) with CUDA events around every
+// launch.  The fastest of each, and the model's choice with its time, go to the cache.
+excmg_status tune_levels(Prob& p, const excmg_options* o, const Ctx& c0) {
+  for (int l = 2; l < (int)p.lv.size(); ++l) {
+    const Grid3 g = p.grid(l);
+    const bool f32 = level_f32(g, l, o);
+    if (tune_lookup(g, f32, nullptr)) continue;
+    excmg_options om = *o;
+    om.autotune = -1;
+    om.profile = 1;
+    om.history = nullptr;
+    om.fixed_iters = nullptr;
+    om.max_iter = 3;
+    om.eps = 1e-300;
+    om.max_refine = 1;
+    om.inner_tol = 1e-30;
+    const Shapes model = level_shapes(g, l, &om);
+    const bool cg_tiled = f32 || g.nodes() > kResidentMaxNodes;
+    // one run: residual + three CG steps at slab depth tz for both; returns the mean
+    // residual launch and the mean CG step (ms)
+    auto run = [&](int tz, double& res_ms, double& step_ms) -> excmg_status {
+      excmg_options ot = om;
+      ot.tile_z = tz;
+      Ctx c = c0;
+      c.defer = false;
+      c.hist = nullptr;
+      long long launches = 0;
+      c.launches = &launches;
+      Prof prof;
+      c.prof = &prof;
+      c.level = l;
+      CK(launch_boundary_init(g, p.gview(l), p.level_u(l), c.s));
+      std::vector<Item> items{make_item(p, l, slot_of(0, l), &ot)};
+      const int fixed = 3;
+      excmg_status e = solve_items(c, items, &ot, state_slots(1), f32 ? nullptr : &fixed);
+      if (e != EXCMG_OK) return e;
+      CK(cudaStreamSynchronize(c.s));
+      std::vector<CGState> hs;
+      e = read_states(c, state_slots(1), hs);
+      if (e != EXCMG_OK) return e;
+      excmg_stats st;
+      memset(&st, 0, sizeof(st));
+      prof.report(&st, hs);
+      res_ms = st.prof_launches[EXCMG_K_RESIDUAL] ? st.prof_ms[EXCMG_K_RESIDUAL] / st.prof_launches[EXCMG_K_RESIDUAL] : 0.0;
+      const int k = f32 ? EXCMG_K_CG_F32 : EXCMG_K_CG_F64;
+      const double steps = items[0].iters > 0 ? items[0].iters : 1;
+      step_ms = st.prof_launches[k] ? st.prof_ms[k] / steps : 0.0;
+      return EXCMG_OK;
+    };
+    excmg_tuning t;
+    memset(&t, 0, sizeof(t));
+    t.N[0] = g.nx;
+    t.N[1] = g.ny;
+    t.N[2] = g.nz;
+    t.f32 = f32 ? 1 : 0;
+    t.res_tz = t.res_tz_model = model.res_tz;
+    t.cg_tz = t.cg_tz_model = cg_tiled ? (f32 ? model.tma_tz : model.cg_tz) : 0;
+    double best_res = 1e300, best_cg = 1e300;
+    std::vector<int> cands = {2, 4, 6, 8, 10, 12, 16, 20, 24, 32, 48};
+    for (int& c : cands)
+      if (f32 && cg_tiled) c = tma_slab_depth(c);  // CG candidates for the tensor-copy engine
+    cands.push_back(model.res_tz);
+    cands.push_back(f32 ? model.tma_tz : model.cg_tz);
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    for (int tz : cands) {
+      if (tz < 1 || tz > g.nz + 1) continue;
+      double rm = 0.0, sm = 0.0;
+      excmg_status e = run(tz, rm, sm);
+      if (e != EXCMG_OK) return e;
+      if (rm > 0 && rm < best_res) {
+        best_res = rm;
+        t.res_tz = tz;
+      }
+      if (tz == model.res_tz) t.res_ms_model = rm;
+      if (cg_tiled && sm > 0) {
+        if (sm < best_cg) {
+          best_cg = sm;
+          t.cg_tz = tz;
+        }
+        if (tz == t.cg_tz_model) t.cg_ms_model = sm;
+      }
+    }
+    t.res_ms = best_res < 1e300 ? best_res : 0.0;
+    t.cg_ms = best_cg < 1e300 ? best_cg : 0.0;
+    if (t.res_ms_model == 0.0) t.res_ms_model = t.res_ms;
+    tune_store(g, f32, t);
+  }
+  return EXCMG_OK;
 }
 
 // The level loop of Algorithm 1 for one or more problems (a single solve is nprob = 1).
@@ -938,6 +1103,10 @@ excmg_status run_excmg(std::vector<Prob>& P, const excmg_options* o, double* u_t
   int maxL = 0;
   for (auto& p : P) maxL = std::max(maxL, (int)p.lv.size());
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned) * np, c.s));
+  if (o->autotune == 1 && np == 1 && !o->fixed_iters) {
+    const excmg_status e = tune_levels(P[0], o, c);
+    if (e != EXCMG_OK) return e;
+  }
   excmg_status result = EXCMG_OK;
   if (stats) {
     for (int i = 0; i < np; ++i) {
@@ -1127,6 +1296,22 @@ void excmg_default_options(excmg_options* o) {
   o->rhs_norm = EXCMG_RHS_NORM_LIFT;
   o->wait_timeout_ms = 0.0;
   o->test_phantom_blocks = 0;
+  o->autotune = 0;
+}
+
+int excmg_tuning_entries(excmg_tuning* out, int max) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  int n = 0;
+  for (const auto& kv : g_tune) {
+    if (out && n < max) out[n] = kv.second;
+    ++n;
+  }
+  return n;
+}
+
+void excmg_tuning_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune.clear();
 }
 
 const char* excmg_status_string(excmg_status s) {

@@ -22,14 +22,20 @@ namespace {
 
 constexpr int kTab = 64;
 
-__device__ void thomas_table(double* cp, double* im, int n) {
+// The factors of the forward sweep written as dp_t = (u_{i+1} - u_{i-1}) A_t + B_t dp_{t-1}
+// (A_t = (1/(2h)) / m_t, B_t = -(1/6) / m_t; the first step's dp_{t-1} is D_0, the
+// last one's carries + D_N: the boundary derivatives moved to the right-hand side), and
+// c'_t of the back substitution.
+__device__ void thomas_table(double* cp, double* A, double* B, int n, double i2h) {
   // a = c = 1/6, b = 4/6
   const double a = 1.0 / 6.0, c = 1.0 / 6.0, b = 4.0 / 6.0;
   double prev = 0.0;
   const int m = n < kTab ? n : kTab;
   for (int t = 0; t < m; ++t) {
     const double piv = (t == 0) ? b : b - a * prev;
-    im[t] = 1.0 / piv;
+    const double im = 1.0 / piv;
+    A[t] = i2h * im;
+    B[t] = -a * im;
     cp[t] = c / piv;
     prev = cp[t];
   }
@@ -47,10 +53,10 @@ __device__ __forceinline__ double d_right(double uN, double u1, double u2, doubl
 __global__ void __launch_bounds__(kThreads)
     k_grad_strided(const double* __restrict__ u, double* __restrict__ out, int N, double h,
                    long long step, int na, int nb, long long sa, long long sb) {
-  __shared__ double cp[kTab], im[kTab];
-  if (threadIdx.x == 0) thomas_table(cp, im, N - 1);
+  __shared__ double cp[kTab], A[kTab], B[kTab];
+  const double ih = 1.0 / h, i2h = 0.5 / h;
+  if (threadIdx.x == 0) thomas_table(cp, A, B, N - 1, i2h);
   __syncthreads();
-  const double ih = 1.0 / h, i2h = 0.5 / h, a6 = 1.0 / 6.0;
   const long long nl = (long long)na * nb;
   for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < nl;
        L += (long long)gridDim.x * blockDim.x) {
@@ -63,14 +69,12 @@ __global__ void __launch_bounds__(kThreads)
     D[0] = D0;
     D[N * step] = DN;
     // forward sweep over unknowns t = 0..N-2 (node i = t + 1)
-    double um = U[0], uc = U[step], dp = 0.0;
+    double um = U[0], uc = U[step], dp = D0;
     for (int i = 1; i <= N - 1; ++i) {
       const double up = U[(long long)(i + 1) * step];
-      double rhs = (up - um) * i2h;
-      if (i == 1) rhs -= a6 * D0;
-      if (i == N - 1) rhs -= a6 * DN;
       const int t = i - 1 < kTab ? i - 1 : kTab - 1;
-      dp = (i == 1) ? rhs * im[0] : (rhs - a6 * dp) * im[t];
+      if (i == N - 1) dp += DN;
+      dp = fma(up - um, A[t], B[t] * dp);
       D[(long long)i * step] = dp;
       um = uc;
       uc = up;
@@ -90,13 +94,13 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(32)
     k_grad_x(const double* __restrict__ u, double* __restrict__ out, int N, double h,
              long long nlines) {
-  __shared__ double cp[kTab], im[kTab];
+  __shared__ double cp[kTab], A[kTab], B[kTab];
   __shared__ double tile[32][35];  // [line][x0-1 .. x0+32]
-  if (threadIdx.x == 0) thomas_table(cp, im, N - 1);
+  const double ih = 1.0 / h, i2h = 0.5 / h;
+  if (threadIdx.x == 0) thomas_table(cp, A, B, N - 1, i2h);
   __syncwarp();
   const int lane = threadIdx.x;
   const long long stride = N + 1;
-  const double ih = 1.0 / h, i2h = 0.5 / h, a6 = 1.0 / 6.0;
   for (long long L0 = (long long)blockIdx.x * 32; L0 < nlines; L0 += (long long)gridDim.x * 32) {
     const long long L = L0 + lane;
     const bool mine = L < nlines;
@@ -109,7 +113,7 @@ __global__ void __launch_bounds__(32)
       out[L * stride + N] = DN;
     }
     // forward sweep, chunk by chunk: unknown nodes i = 1..N-1
-    double dp = 0.0;
+    double dp = D0;
     for (int x0 = 1; x0 <= N - 1; x0 += 32) {
       const int cnt = min(32, N - x0);  // nodes x0 .. x0+cnt-1
       __syncwarp();
@@ -122,11 +126,9 @@ __global__ void __launch_bounds__(32)
       if (mine) {
         for (int c = 0; c < cnt; ++c) {
           const int i = x0 + c;
-          double rhs = (tile[lane][c + 2] - tile[lane][c]) * i2h;
-          if (i == 1) rhs -= a6 * D0;
-          if (i == N - 1) rhs -= a6 * DN;
           const int t = i - 1 < kTab ? i - 1 : kTab - 1;
-          dp = (i == 1) ? rhs * im[0] : (rhs - a6 * dp) * im[t];
+          if (i == N - 1) dp += DN;
+          dp = fma(tile[lane][c + 2] - tile[lane][c], A[t], B[t] * dp);
           tile[lane][c] = dp;
         }
       }

@@ -237,31 +237,52 @@ __global__ void __launch_bounds__(kThreads) k_exp_finite_one(ProlongDesc d, long
 
 // EXP_true: u~ = u_h + (1/15) (mean of d = u_h - u_2h over the grid-2h corners of the
 // edge / face / element the node is the centre of; d itself at grid-2h nodes).
+// EXP_true tiles: 64 x 8 x 2 fine nodes per block, whose grid-2h corners are the
+// 33 x 5 x 2 coarse nodes from (x0/2, y0/2, z0/2).
+constexpr int kEtX = 64, kEtY = 8, kEtZ = 2;
+constexpr int kEcX = kEtX / 2 + 1, kEcY = kEtY / 2 + 1, kEcZ = kEtZ / 2 + 1;
+
 __global__ void __launch_bounds__(kThreads)
     k_exp_true(Grid3 g, const double* __restrict__ uh, const double* __restrict__ u2h,
-               double* __restrict__ ut) {
-  const long long n = g.nodes();
-  const int n1x = g.nx / 2, n1y = g.ny / 2;
+               double* __restrict__ ut, int ntx, int nty) {
+  // EXP_true (eqs. t1, chenlin): u~ = u_h + (1/15) x (mean of d over the grid-2h corners
+  // of the node's edge, face or cell), d = u_h - u_2h at grid-2h nodes (a grid-2h node is
+  // its own corner).  The block forms d at the coarse corners of its tile once, in
+  // shared memory; every node then sums d at 8 = 2 x 2 x 2 points, the corners
+  // (I, I + ox) x (J, J + oy) x (K, K + oz) (ox, oy, oz the parities of i, j, k): where
+  // a parity is 0 the two choices coincide, each distinct corner appears equally often,
+  // and sum / 8 is the mean over the distinct corners exactly (duplicates only scale
+  // by powers of two).
+  __shared__ double D[kEcZ][kEcY][kEcX];
+  const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
+  const int x0 = bx * kEtX, y0 = by * kEtY, z0 = bz * kEtZ;
+  const int I0 = x0 / 2, J0 = y0 / 2, K0 = z0 / 2;
+  const int n1x = g.nx / 2, n1y = g.ny / 2, n1z = g.nz / 2;
   const long long s1y = n1x + 1, s1z = (long long)(n1x + 1) * (n1y + 1);
-  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n;
-       o += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(o % g.sy);
-    const int j = (int)((o / g.sy) % (g.ny + 1));
-    const int k = (int)(o / g.sz);
-    const int ox = i & 1, oy = j & 1, oz = k & 1;
-    const int cx = i >> 1, cy = j >> 1, cz = k >> 1;
-    double sum = 0.0;
-    for (int a = 0; a <= oz; ++a)
-      for (int b = 0; b <= oy; ++b)
-        for (int c = 0; c <= ox; ++c) {
-          const int I = cx + c, J = cy + b, K = cz + a;
-          sum += uh[2 * I + 2 * J * g.sy + 2LL * K * g.sz] - u2h[I + J * s1y + K * s1z];
-        }
-    // (1/15) * mean over the corners; the reciprocals are compile-time constants
-    const double inv = (ox + oy + oz == 0) ? 1.0 / 15.0
-                     : (ox + oy + oz == 1) ? 1.0 / 30.0
-                     : (ox + oy + oz == 2) ? 1.0 / 60.0 : 1.0 / 120.0;
-    ut[o] = fma(sum, inv, uh[o]);
+  for (int e = threadIdx.x; e < kEcX * kEcY * kEcZ; e += kThreads) {
+    const int a = e % kEcX, b = (e / kEcX) % kEcY, c = e / (kEcX * kEcY);
+    const int I = I0 + a, J = J0 + b, K = K0 + c;
+    double dv = 0.0;
+    if (I <= n1x && J <= n1y && K <= n1z)
+      dv = uh[2LL * I + 2LL * J * g.sy + 2LL * K * g.sz] - u2h[I + J * s1y + K * s1z];
+    D[c][b][a] = dv;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kEtX, tq = threadIdx.x / kEtX;  // tq = 0 .. 3
+  const int i = x0 + tx;
+  if (i > g.nx) return;  // no barrier below
+  const int ox = i & 1, ia = (i >> 1) - I0;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int jl = tq + 4 * (m & 1), kl = m >> 1;
+    const int j = y0 + jl, k = z0 + kl;
+    if (j > g.ny || k > g.nz) continue;
+    const int oy = j & 1, oz = k & 1, ja = (j >> 1) - J0, ka = (k >> 1) - K0;
+    const double s0 = (D[ka][ja][ia] + D[ka][ja][ia + ox]) + (D[ka][ja + oy][ia] + D[ka][ja + oy][ia + ox]);
+    const double s1 = (D[ka + oz][ja][ia] + D[ka + oz][ja][ia + ox]) +
+                      (D[ka + oz][ja + oy][ia] + D[ka + oz][ja + oy][ia + ox]);
+    const long long o = i + (long long)j * g.sy + (long long)k * g.sz;
+    ut[o] = fma(s0 + s1, 1.0 / 120.0, uh[o]);  // (1/15) x (1/8)
   }
 }
 
@@ -312,9 +333,18 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Blocks of a grid-stride elementwise launch over n items: at most 16 per SM of the
+// current device.
 int flat_grid(long long n) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
   long long b = (n + kThreads - 1) / kThreads;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > (long long)sms * 16) b = (long long)sms * 16;
   return b < 1 ? 1 : (int)b;
 }
 
@@ -367,7 +397,11 @@ cudaError_t launch_exp_finite_one(const ProlongDesc& d, cudaStream_t s) {
 
 cudaError_t launch_exp_true(const Grid3& g, const double* uh, const double* u2h, double* ut,
                             cudaStream_t s) {
-  k_exp_true<<<flat_grid(g.nodes()), kThreads, 0, s>>>(g, uh, u2h, ut);
+  const int ntx = (g.nx + 1 + kEtX - 1) / kEtX, nty = (g.ny + 1 + kEtY - 1) / kEtY;
+  const long long ntz = (g.nz + 1 + kEtZ - 1) / kEtZ;
+  const long long blocks = (long long)ntx * nty * ntz;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_exp_true<<<(unsigned)blocks, kThreads, 0, s>>>(g, uh, u2h, ut, ntx, nty);
   return cudaGetLastError();
 }
 

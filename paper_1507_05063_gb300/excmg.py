@@ -49,7 +49,15 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_int), ("dsolve", ctypes.c_int), ("eps_ratio", ctypes.c_double),
                 ("prolong", ctypes.c_int), ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_len", ctypes.c_int), ("rhs_norm", ctypes.c_int),
-                ("wait_timeout_ms", ctypes.c_double), ("test_phantom_blocks", ctypes.c_int)]
+                ("wait_timeout_ms", ctypes.c_double), ("test_phantom_blocks", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int * 3), ("f32", ctypes.c_int), ("res_tz", ctypes.c_int),
+                ("res_tz_model", ctypes.c_int), ("res_ms", ctypes.c_double),
+                ("res_ms_model", ctypes.c_double), ("cg_tz", ctypes.c_int), ("cg_tz_model", ctypes.c_int),
+                ("cg_ms", ctypes.c_double), ("cg_ms_model", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -110,12 +118,25 @@ excmg_cg = _sig("excmg_cg", ctypes.c_int, [_GP, _P, _OP, _P, _P, ctypes.c_size_t
 excmg_residual = _sig("excmg_residual", ctypes.c_int,
                       [_GP, _P, _P, _P, _D, _D, _P, ctypes.c_size_t, _P])
 excmg_cg_noalloc = _sig("excmg_cg_noalloc", ctypes.c_int, [_GP, _P, _OP, _P, _SP, _P])
+excmg_tuning_entries = _sig("excmg_tuning_entries", ctypes.c_int, [ctypes.POINTER(Tuning), ctypes.c_int])
+excmg_tuning_clear = _sig("excmg_tuning_clear", None, [])
 
 EXPORTED = ["excmg_default_options", "excmg_status_string", "excmg_num_levels",
             "excmg_workspace_size", "excmg_workspace_size_batched",
             "excmg_workspace_size_adjoint", "excmg_workspace_size_level", "excmg_solve", "excmg_grad", "excmg_solve_batched",
             "excmg_adjoint", "excmg_exp_finite", "excmg_exp_true", "excmg_cg", "excmg_residual",
-            "excmg_cg_noalloc"]
+            "excmg_cg_noalloc", "excmg_tuning_entries", "excmg_tuning_clear"]
+
+
+def tuning_entries():
+    """The launch-shape cache (options.autotune) as a list of dicts."""
+    n = excmg_tuning_entries(None, 0)
+    arr = (Tuning * max(n, 1))()
+    n = excmg_tuning_entries(arr, n)
+    return [{"N": list(t.N), "f32": t.f32, "res_tz": t.res_tz, "res_tz_model": t.res_tz_model,
+             "res_ms": t.res_ms, "res_ms_model": t.res_ms_model, "cg_tz": t.cg_tz,
+             "cg_tz_model": t.cg_tz_model, "cg_ms": t.cg_ms, "cg_ms_model": t.cg_ms_model}
+            for t in arr[:n]]
 
 
 class ExcmgError(RuntimeError):
@@ -143,7 +164,7 @@ RHS_NORM = {"lift": 0, "forcing": 1}
 def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
                  inner_tol=1e-4, max_refine=50, fixed_iters=None, tile_z=0, chunk=0, profile=0,
                  mixed_min_nodes=0, dsolve="direct", eps_ratio=1.0, prolong="quartic", history=0,
-                 rhs_norm="lift", wait_timeout_ms=0.0, test_phantom_blocks=0):
+                 rhs_norm="lift", wait_timeout_ms=0.0, test_phantom_blocks=0, autotune=0):
     o = Options()
     excmg_default_options(ctypes.byref(o))
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else int(precision)
@@ -162,6 +183,7 @@ def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
     o.rhs_norm = RHS_NORM[rhs_norm] if isinstance(rhs_norm, str) else int(rhs_norm)
     o.wait_timeout_ms = float(wait_timeout_ms)
     o.test_phantom_blocks = int(test_phantom_blocks)
+    o.autotune = int(autotune)
     keep = {}
     if fixed_iters is not None:
         keep["fixed"] = (ctypes.c_int * len(fixed_iters))(*[int(v) for v in fixed_iters])

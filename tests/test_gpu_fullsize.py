@@ -143,3 +143,21 @@ def test_1024x512x512_exp_finite_sampled_cells(X, c3):
         got = w[8 * cz:8 * cz + 9, 8 * cy:8 * cy + 9, 8 * cx:8 * cx + 9]
         assert np.max(np.abs(got - want)) <= 1e-12 * max(np.max(np.abs(want)), 1e-300)
     assert N1[0] == 512 and N2[0] == 256
+
+
+def test_1024x512x512_fp64_matches_oracle_record(X, c3):
+    """The FP64 solve of the full 1024x512x512 workload against the oracle's complete
+    solve of it (tests/golden/oracle_c3.txt, written by make_oracle_c3.py): the same CG
+    step count on every level (+-1) and the same errors against the exact solution
+    (0.1%)."""
+    N, N0, L, f, g, u, fd, gd = c3
+    rec = {}
+    from conftest import read_golden
+    for row in read_golden("oracle_c3.txt"):
+        rec[row[0]] = row[1]
+    iters = [int(v) for v in rec["iters"].split(",")]
+    res = X.solve(fd, gd, L, N0, eps=1e-9, eps_coarse=1e-12)
+    assert all(abs(a - b) <= 1 for a, b in zip(res["stats"]["iters"], iters)), (res["stats"]["iters"], iters)
+    uh = res["u"].cpu().numpy()
+    assert np.sqrt(np.mean((uh - u) ** 2)) == pytest.approx(float(rec["err_L2"]), rel=1e-3)
+    assert np.max(np.abs(uh - u)) == pytest.approx(float(rec["err_Linf"]), rel=1e-3)

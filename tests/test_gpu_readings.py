@@ -167,3 +167,35 @@ def test_max_iter_zero_reports_not_converged(X):
     X.cg(dev(f), u, L, eps=1e-9)
     st = X.cg(dev(f), u, L, eps=1e-9, max_iter=0)
     assert st["status"] == "EXCMG_OK" and st["iters"][0] == 0
+
+
+# ------------------------------------------------------------------ launch-shape tuning
+
+def test_autotune_fills_cache_and_keeps_the_solution(X):
+    """options.autotune = 1 times candidate slab depths for every level from 2 up and
+    caches the fastest per (grid, engine class, device); later solves (autotune = 0) use
+    the cache.  The tuned and the modelled launch shapes solve the same problem to the
+    same tolerance with the same error against the exact solution (+-1%)."""
+    N, N0, L = (256, 128, 64), (8, 4, 2), (1.0, 1.0, 1.0)
+    f, g, u = P.make_inputs(P.PROBLEMS["exp3"], N)
+    fd, gd = dev(f), dev(g)
+    X.excmg_tuning_clear()
+    for prec in ("fp64", "mixed"):
+        kw = dict(eps=1e-10, precision=prec, mixed_min_nodes=1 << 16)
+        ref = X.solve(fd, gd, L, N0, autotune=-1, **kw)
+        X.solve(fd, gd, L, N0, autotune=1, **kw)
+        ents = [e for e in X.tuning_entries() if e["f32"] == (1 if prec == "mixed" else 0)]
+        assert ents, prec
+        for e in ents:
+            assert e["res_tz"] >= 1 and e["res_ms"] > 0 and e["res_ms"] <= e["res_ms_model"] * 1.0001
+            if e["cg_tz"]:
+                assert e["cg_ms"] > 0 and e["cg_ms"] <= e["cg_ms_model"] * 1.0001
+        tuned = X.solve(fd, gd, L, N0, **kw)
+        assert all(r <= 1e-10 * 1.0000001 for r in tuned["stats"]["relres"][2:])
+        e_ref = np.max(np.abs(host(ref["u"]) - u))
+        e_tun = np.max(np.abs(host(tuned["u"]) - u))
+        assert e_tun == pytest.approx(e_ref, rel=1e-2)
+    levels = {tuple(e["N"]) for e in X.tuning_entries()}
+    assert (256, 128, 64) in levels and (64, 32, 16) in levels
+    X.excmg_tuning_clear()
+    assert X.tuning_entries() == []
