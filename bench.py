@@ -659,9 +659,10 @@ def utilde_grad_rates(X, torch, u_dev, L, hbm_peak, reps=5):
     return out
 
 
-def extra_c2(X, torch, stream):
-    """The 512x256x128 workload: FP64 and MIXED solves, per-level tolerance, and the
-    prolongation ablation (what EXP_finite saves)."""
+def extra_c2(X, torch, stream, hbm_peak, cg_finest):
+    """The 512x256x128 workload: FP64 and MIXED solves (after their tuning pass), the
+    finest-grid CG step rates, per-level tolerance, and the prolongation ablation (what
+    EXP_finite saves)."""
     name, L, N, N0, eps, epsc, _ = WORKLOADS["c2"]
     f, g, u = P.make_inputs(P.PROBLEMS[name], N)
     fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
@@ -671,6 +672,11 @@ def extra_c2(X, torch, stream):
     for prec in ("fp64", "mixed"):
         kw = dict(eps=eps, eps_coarse=epsc, precision=prec)
         ws = X.workspace(X.solve_workspace_bytes(L, N, N0, **kw), fd.device)
+        X.solve(fd, gd, L, N0, ws=ws, out=ud, autotune=1, **kw)
+        # the float32 engine's shapes for this grid: a MIXED tuning solve with float32 CG
+        # on every level from 2 up
+        X.solve(fd, gd, L, N0, out=ud, autotune=1, precision="mixed", mixed_min_nodes=1, eps=eps,
+                eps_coarse=epsc)
         for _ in range(3):
             X.solve(fd, gd, L, N0, ws=ws, out=ud, **kw)
         ms, res, _ = timed_solves(X, torch, stream, 10, fd, gd, L, N0, ws, ud, **kw)
@@ -696,6 +702,8 @@ def extra_c2(X, torch, stream):
         tol[tag] = {"ms_per_solve": a.elapsed_time(b) / 3, "iters_per_level": r2["stats"]["iters"],
                     "u_Linf": float(np.max(np.abs(uh2 - u))), "u_tilde_Linf": float(np.max(np.abs(ut2 - u)))}
     out["tolerance_per_level"] = tol
+    if "512x256x128" not in cg_finest:
+        cg_finest["512x256x128"] = cg_rates(X, torch, "c2", hbm_peak)
     abl = {}
     for kind in ("quartic", "quadratic", "linear"):
         o2 = dict(eps=eps, eps_coarse=epsc, precision="fp64", prolong=kind)
@@ -885,6 +893,14 @@ def main():
     stream = torch.cuda.current_stream()
     ranks = Replicas(world, device, dist if world > 1 else None)
 
+    # the launch-shape tuning pass (options.autotune = 1) for both precisions' levels, once;
+    # every later solve uses its cache
+    other = "fp64" if prec == "mixed" else "mixed"
+    o_opts = dict(opts, precision=other)
+    ws_o = X.workspace(X.solve_workspace_bytes(L, N, N0, **o_opts), device)
+    uo = torch.empty_like(fd)
+    X.solve(fd, gd, L, N0, ws=ws, out=ud, autotune=1, **opts)
+    X.solve(fd, gd, L, N0, ws=ws_o, out=uo, autotune=1, **o_opts)
     for _ in range(max(args.warmup, 0)):
         X.solve(fd, gd, L, N0, ws=ws, out=ud, **opts)
 
@@ -902,11 +918,18 @@ def main():
     uh = ud.cpu().numpy()
     err = errors(uh, u_exact)
 
+    # ---- profiled repeat (events around every launch; not the timed region) and the
+    # finest-grid CG step rates, in the memory state of the timed region
+    prof = X.solve(fd, gd, L, N0, ws=ws, out=ud, profile=1, **opts)["stats"]["profile"]
+    hbm_peak, peak_kind = load_peaks()
+    cg_finest = {}
+    if not args.no_extras and wl in ("c3", "c2"):
+        try:
+            cg_finest[{"c3": "1024x512x512", "c2": "512x256x128"}[wl]] = cg_rates(X, torch, wl, hbm_peak)
+        except Exception as ex:  # keep the line; record what failed
+            cg_finest["error"] = repr(ex)
+
     # ---- the other precision at the same tolerance, and the discretisation error
-    other = "fp64" if prec == "mixed" else "mixed"
-    o_opts = dict(opts, precision=other)
-    ws_o = X.workspace(X.solve_workspace_bytes(L, N, N0, **o_opts), device)
-    uo = torch.empty_like(fd)
     for _ in range(2):
         X.solve(fd, gd, L, N0, ws=ws_o, out=uo, **o_opts)
     k_o = max(3, args.steps // 4)
@@ -946,9 +969,6 @@ def main():
     # ---- end to end through the C-ABI with host buffers
     e2e = e2e_modes(X, torch, args, stream, f, g, L, N0, ws, fd, uh, opts, ranks)
 
-    # ---- profiled repeat (events around every launch; not the timed region)
-    prof = X.solve(fd, gd, L, N0, ws=ws, out=ud, profile=1, **opts)["stats"]["profile"]
-    hbm_peak, peak_kind = load_peaks()
     kernels = kernel_table(prof, hbm_peak)
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     roof = roofline_of(dom, kernels[dom], prof, hbm_peak, peak_kind, wl)
@@ -976,19 +996,15 @@ def main():
     del e2e
 
     if not args.no_extras:
-        extras = {}
-        try:
-            extras["cg_finest"] = {"1024x512x512": cg_rates(X, torch, "c3", hbm_peak),
-                                   "512x256x128": cg_rates(X, torch, "c2", hbm_peak)}
-        except Exception as ex:  # keep the line; record what failed
-            extras["cg_finest"] = {"error": repr(ex)}
+        extras = {"cg_finest": cg_finest}
         try:
             extras["utilde_and_gradient"] = utilde_grad_rates(X, torch, ud, L, hbm_peak)
         except Exception as ex:
             extras["utilde_and_gradient"] = {"error": repr(ex)}
         del ws
         torch.cuda.empty_cache()
-        for key, fn in (("c2", lambda: extra_c2(X, torch, stream)), ("c1", lambda: extra_c1(X, torch, stream)),
+        for key, fn in (("c2", lambda: extra_c2(X, torch, stream, hbm_peak, cg_finest)),
+                        ("c1", lambda: extra_c1(X, torch, stream)),
                         ("c4_batched", lambda: run_batched(X, torch)), ("c5_adjoint", lambda: run_adjoint(X, torch))):
             try:
                 extras[key] = fn()
@@ -996,6 +1012,10 @@ def main():
                 extras[key] = {"error": repr(ex)}
             torch.cuda.empty_cache()
         line["extras"] = extras
+    line["tuning"] = {"how": "options.autotune = 1 on the first solve of each workload and precision: "
+                             "candidate slab depths per level timed with CUDA events, the fastest cached "
+                             "per (level grid, engine class, device) and used by every later solve",
+                      "levels": X.tuning_entries()}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and wl == "c3":
         line["cpu_baseline"] = cpu_baseline_c3()

@@ -1407,6 +1407,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 Tiling make_tma_tiling(const Grid3& g, int tz) {
+  if (tz < 1) tz = 1;
   Tiling t;
   t.tz = tz;
   t.ntx = (g.nx + 1 + kTX - 1) / kTX;

@@ -48,6 +48,7 @@ Coef make_coef(const Grid3& g) {
 }
 
 Tiling make_tiling(const Grid3& g, int tz) {
+  if (tz < 1) tz = 1;
   Tiling t;
   t.tz = tz;
   t.ntx = (g.nx + 1 + kTX - 1) / kTX;
@@ -330,6 +331,7 @@ Header header_layout(int nprob) {
 
 // One problem's static data for a solve.
 struct Prob {
+  bool cascade = true;   // levels of Algorithm 1 (0 and 1: DSOLVE); false: one CG grid
   std::vector<Level> lv;
   excmg_grid gr;
   const double* f;
@@ -899,10 +901,10 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
   }
 }
 
-// The engine class of level grid g under options o: true when its CG runs in float32
-// (MIXED inner solves; DSOLVE levels are float64).
-bool level_f32(const Grid3& g, int l, const excmg_options* o) {
-  return o->precision == EXCMG_MIXED && g.nodes() >= mixed_min(o) && l >= 2;
+// The engine class of a level grid g under options o: true when its CG runs in float32
+// (MIXED inner solves; the DSOLVE levels 0 and 1 of a cascade are float64).
+bool level_f32(const Grid3& g, bool dsolve_level, const excmg_options* o) {
+  return o->precision == EXCMG_MIXED && g.nodes() >= mixed_min(o) && !dsolve_level;
 }
 
 // Launch shapes of a level: the caller's tile_z, else the tuned ones (options.autotune
@@ -910,26 +912,30 @@ bool level_f32(const Grid3& g, int l, const excmg_options* o) {
 struct Shapes {
   int res_tz, cg_tz, tma_tz;
 };
-Shapes level_shapes(const Grid3& g, int l, const excmg_options* o) {
+Shapes level_shapes(const Grid3& g, bool dsolve_level, const excmg_options* o) {
   Shapes sh;
   const int tz = choose_tz(g, persistent_grid(1LL << 40), o->tile_z);
   sh.cg_tz = tz;
   sh.tma_tz = o->tile_z > 0 ? tz : tma_slab_depth(tz);
   sh.res_tz = choose_res_tz(g, residual_grid(1LL << 40), o->tile_z);
   excmg_tuning t;
-  if (o->tile_z == 0 && o->autotune >= 0 && tune_lookup(g, level_f32(g, l, o), &t)) {
-    sh.res_tz = t.res_tz;
-    if (level_f32(g, l, o))
-      sh.tma_tz = t.cg_tz;
-    else
-      sh.cg_tz = t.cg_tz;
+  if (o->tile_z == 0 && o->autotune >= 0 && tune_lookup(g, level_f32(g, dsolve_level, o), &t)) {
+    // an entry's cg_tz is 0 where the single solve's engine for the grid is not tiled
+    // (resident or cluster): the model's depth stays for the tiled engines of a batch
+    if (t.res_tz > 0) sh.res_tz = t.res_tz;
+    if (t.cg_tz > 0) {
+      if (level_f32(g, dsolve_level, o))
+        sh.tma_tz = t.cg_tz;
+      else
+        sh.cg_tz = t.cg_tz;
+    }
   }
   return sh;
 }
 
 Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   const Grid3 g = p.grid(l);
-  const Shapes sh = level_shapes(g, l, o);
+  const Shapes sh = level_shapes(g, p.cascade && l < 2, o);
   const int tz = sh.cg_tz;
   const Tiling t = make_tiling(g, tz);
   Item it;
@@ -989,7 +995,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
 excmg_status tune_levels(Prob& p, const excmg_options* o, const Ctx& c0) {
   for (int l = 2; l < (int)p.lv.size(); ++l) {
     const Grid3 g = p.grid(l);
-    const bool f32 = level_f32(g, l, o);
+    const bool f32 = level_f32(g, false, o);
     if (tune_lookup(g, f32, nullptr)) continue;
     excmg_options om = *o;
     om.autotune = -1;
@@ -1000,7 +1006,7 @@ excmg_status tune_levels(Prob& p, const excmg_options* o, const Ctx& c0) {
     om.eps = 1e-300;
     om.max_refine = 1;
     om.inner_tol = 1e-30;
-    const Shapes model = level_shapes(g, l, &om);
+    const Shapes model = level_shapes(g, false, &om);
     const bool cg_tiled = f32 || g.nodes() > kResidentMaxNodes;
     // one run: residual + three CG steps at slab depth tz for both; returns the mean
     // residual launch and the mean CG step (ms)
@@ -1484,6 +1490,7 @@ excmg_status excmg_cg(const excmg_grid* grid, const double* f, const excmg_optio
   c.H = header_layout(1);
   c.s = static_cast<cudaStream_t>(stream);
   Prob p;
+  p.cascade = false;
   p.lv = lv;
   p.gr = *grid;
   p.f = f;
@@ -1588,6 +1595,7 @@ excmg_status excmg_adjoint(const excmg_grid* grid, const double* dLdu, const exc
   // lambda lives in front of the level vectors; it starts at zero (zero boundary too)
   double* lam = reinterpret_cast<double*>(c.ws + c.H.bytes);
   Prob p;
+  p.cascade = false;
   p.lv = std::vector<Level>{{grid->Nx, grid->Ny, grid->Nz}};
   p.gr = *grid;
   p.f = nullptr;

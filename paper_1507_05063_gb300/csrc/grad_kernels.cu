@@ -49,7 +49,11 @@ __device__ __forceinline__ double d_right(double uN, double u1, double u2, doubl
 }
 
 // Lines along a strided direction: node t of line L is base(L) + t * step.  Lines are
-// indexed by (a, b) with a fastest: base = a * sa + b * sb.
+// indexed by (a, b) with a fastest: base = a * sa + b * sb.  A thread runs two lines,
+// L and L + half (half = ceil(lines / 2)): two independent recurrences interleaved, so
+// the dependent FP64 operations of one overlap the other's (each step of the forward
+// sweep is a product and an FMA on the previous step's value); neighbouring threads
+// still take neighbouring a, so every step stays a coalesced row access.
 __global__ void __launch_bounds__(kThreads)
     k_grad_strided(const double* __restrict__ u, double* __restrict__ out, int N, double h,
                    long long step, int na, int nb, long long sa, long long sb) {
@@ -57,34 +61,58 @@ __global__ void __launch_bounds__(kThreads)
   const double ih = 1.0 / h, i2h = 0.5 / h;
   if (threadIdx.x == 0) thomas_table(cp, A, B, N - 1, i2h);
   __syncthreads();
-  const long long nl = (long long)na * nb;
-  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < nl;
+  const long long nl = (long long)na * nb, half = (nl + 1) / 2;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < half;
        L += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(L % na), b = (int)(L / na);
-    const double* __restrict__ U = u + a * sa + b * sb;
-    double* __restrict__ D = out + a * sa + b * sb;
-    const double D0 = d_left(U[0], U[step], U[2 * step], U[3 * step], U[4 * step], ih);
-    const double DN = d_right(U[N * step], U[(N - 1) * step], U[(N - 2) * step], U[(N - 3) * step],
-                              U[(N - 4) * step], ih);
-    D[0] = D0;
-    D[N * step] = DN;
+    const bool two = L + half < nl;
+    const long long L1 = two ? L + half : L;  // the second line (a copy of the first if none)
+    const double* __restrict__ U0 = u + (L % na) * sa + (L / na) * sb;
+    const double* __restrict__ U1 = u + (L1 % na) * sa + (L1 / na) * sb;
+    double* __restrict__ D0p = out + (L % na) * sa + (L / na) * sb;
+    double* __restrict__ D1p = out + (L1 % na) * sa + (L1 / na) * sb;
+    const double a0 = d_left(U0[0], U0[step], U0[2 * step], U0[3 * step], U0[4 * step], ih);
+    const double a1 = d_left(U1[0], U1[step], U1[2 * step], U1[3 * step], U1[4 * step], ih);
+    const double n0 = d_right(U0[N * step], U0[(N - 1) * step], U0[(N - 2) * step], U0[(N - 3) * step],
+                              U0[(N - 4) * step], ih);
+    const double n1 = d_right(U1[N * step], U1[(N - 1) * step], U1[(N - 2) * step], U1[(N - 3) * step],
+                              U1[(N - 4) * step], ih);
+    D0p[0] = a0;
+    D0p[N * step] = n0;
+    if (two) {
+      D1p[0] = a1;
+      D1p[N * step] = n1;
+    }
     // forward sweep over unknowns t = 0..N-2 (node i = t + 1)
-    double um = U[0], uc = U[step], dp = D0;
+    double um0 = U0[0], uc0 = U0[step], dp0 = a0;
+    double um1 = U1[0], uc1 = U1[step], dp1 = a1;
     for (int i = 1; i <= N - 1; ++i) {
-      const double up = U[(long long)(i + 1) * step];
+      const long long o = (long long)(i + 1) * step;
+      const double up0 = U0[o], up1 = U1[o];
       const int t = i - 1 < kTab ? i - 1 : kTab - 1;
-      if (i == N - 1) dp += DN;
-      dp = fma(up - um, A[t], B[t] * dp);
-      D[(long long)i * step] = dp;
-      um = uc;
-      uc = up;
+      if (i == N - 1) {
+        dp0 += n0;
+        dp1 += n1;
+      }
+      dp0 = fma(up0 - um0, A[t], B[t] * dp0);
+      dp1 = fma(up1 - um1, A[t], B[t] * dp1);
+      D0p[(long long)i * step] = dp0;
+      if (two) D1p[(long long)i * step] = dp1;
+      um0 = uc0;
+      uc0 = up0;
+      um1 = uc1;
+      uc1 = up1;
     }
     // back substitution
-    double x = dp;
+    double x0 = dp0, x1 = dp1;
     for (int i = N - 2; i >= 1; --i) {
       const int t = i - 1 < kTab ? i - 1 : kTab - 1;
-      x = D[(long long)i * step] - cp[t] * x;
-      D[(long long)i * step] = x;
+      const long long o = (long long)i * step;
+      x0 = D0p[o] - cp[t] * x0;
+      D0p[o] = x0;
+      if (two) {
+        x1 = D1p[o] - cp[t] * x1;
+        D1p[o] = x1;
+      }
     }
   }
 }
@@ -188,12 +216,12 @@ cudaError_t launch_grad(const Grid3& g, const double* u, double* ux, double* uy,
                         cudaStream_t s) {
   const long long nlx = (long long)(g.ny + 1) * (g.nz + 1);
   k_grad_x<<<grid_for(nlx, 32), 32, 0, s>>>(u, ux, g.nx, g.hx, nlx);
-  // y-lines: a = i (fastest), b = k
-  k_grad_strided<<<grid_for((long long)(g.nx + 1) * (g.nz + 1), kThreads), kThreads, 0, s>>>(
+  // y-lines: a = i (fastest), b = k; two lines per thread
+  k_grad_strided<<<grid_for(((long long)(g.nx + 1) * (g.nz + 1) + 1) / 2, kThreads), kThreads, 0, s>>>(
       u, uy, g.ny, g.hy, g.sy, g.nx + 1, g.nz + 1, 1, g.sz);
   // z-lines: a = i + sy*j flattened (fastest), b unused
-  k_grad_strided<<<grid_for(g.sz, kThreads), kThreads, 0, s>>>(u, uz, g.nz, g.hz, g.sz,
-                                                              (int)g.sz, 1, 1, 0);
+  k_grad_strided<<<grid_for((g.sz + 1) / 2, kThreads), kThreads, 0, s>>>(u, uz, g.nz, g.hz, g.sz,
+                                                                        (int)g.sz, 1, 1, 0);
   return cudaGetLastError();
 }
 

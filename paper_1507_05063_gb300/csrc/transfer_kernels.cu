@@ -248,11 +248,12 @@ __global__ void __launch_bounds__(kThreads)
   // EXP_true (eqs. t1, chenlin): u~ = u_h + (1/15) x (mean of d over the grid-2h corners
   // of the node's edge, face or cell), d = u_h - u_2h at grid-2h nodes (a grid-2h node is
   // its own corner).  The block forms d at the coarse corners of its tile once, in
-  // shared memory; every node then sums d at 8 = 2 x 2 x 2 points, the corners
-  // (I, I + ox) x (J, J + oy) x (K, K + oz) (ox, oy, oz the parities of i, j, k): where
-  // a parity is 0 the two choices coincide, each distinct corner appears equally often,
-  // and sum / 8 is the mean over the distinct corners exactly (duplicates only scale
-  // by powers of two).
+  // shared memory.  A node sums d over its corner rows (J, J + oy) x (K, K + oz) -- oy
+  // and oz are the same in every lane of a warp (a warp owns fixed rows and planes of
+  // the tile), so these branches do not diverge and only existing corners cost FP64
+  // instructions (GB300 issues few) -- at the two corner columns I and I + ox; for even
+  // i both columns are I, and the sum of the two counts it twice, so the mean over the
+  // distinct corners is (e_I + e_{I+ox}) / (2 nrows) in every lane.
   __shared__ double D[kEcZ][kEcY][kEcX];
   const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
   const int x0 = bx * kEtX, y0 = by * kEtY, z0 = bz * kEtZ;
@@ -278,11 +279,25 @@ __global__ void __launch_bounds__(kThreads)
     const int j = y0 + jl, k = z0 + kl;
     if (j > g.ny || k > g.nz) continue;
     const int oy = j & 1, oz = k & 1, ja = (j >> 1) - J0, ka = (k >> 1) - K0;
-    const double s0 = (D[ka][ja][ia] + D[ka][ja][ia + ox]) + (D[ka][ja + oy][ia] + D[ka][ja + oy][ia + ox]);
-    const double s1 = (D[ka + oz][ja][ia] + D[ka + oz][ja][ia + ox]) +
-                      (D[ka + oz][ja + oy][ia] + D[ka + oz][ja + oy][ia + ox]);
+    double e0 = D[ka][ja][ia], e1 = D[ka][ja][ia + ox];
+    if (oy) {  // uniform in the warp
+      e0 += D[ka][ja + 1][ia];
+      e1 += D[ka][ja + 1][ia + ox];
+    }
+    if (oz) {
+      double f0 = D[ka + 1][ja][ia], f1 = D[ka + 1][ja][ia + ox];
+      if (oy) {
+        f0 += D[ka + 1][ja + 1][ia];
+        f1 += D[ka + 1][ja + 1][ia + ox];
+      }
+      e0 += f0;
+      e1 += f1;
+    }
+    // (1/15) x 1 / (2 x the number of corner rows): compile-time constants
+    const int nrows = (1 + oy) * (1 + oz);
+    const double w = nrows == 1 ? 1.0 / 30.0 : (nrows == 2 ? 1.0 / 60.0 : 1.0 / 120.0);
     const long long o = i + (long long)j * g.sy + (long long)k * g.sz;
-    ut[o] = fma(s0 + s1, 1.0 / 120.0, uh[o]);  // (1/15) x (1/8)
+    ut[o] = fma(e0 + e1, w, uh[o]);
   }
 }
 

@@ -197,5 +197,13 @@ def test_autotune_fills_cache_and_keeps_the_solution(X):
         assert e_tun == pytest.approx(e_ref, rel=1e-2)
     levels = {tuple(e["N"]) for e in X.tuning_entries()}
     assert (256, 128, 64) in levels and (64, 32, 16) in levels
+    # a batch over tuned grids (some of whose single-solve CG engines are untiled, cached
+    # without a CG slab depth) solves as the single solve does
+    kw = dict(eps=1e-10, precision="fp64")
+    single = X.solve(fd, gd, L, N0, **kw)
+    bat = X.solve_batched([X.BatchedProblem(L, N, N0, fd, gd)] * 2, **kw)
+    assert bat["status"] == "EXCMG_OK"
+    for ub in bat["u"]:
+        assert np.max(np.abs(host(ub) - u)) == pytest.approx(np.max(np.abs(host(single["u"]) - u)), rel=1e-2)
     X.excmg_tuning_clear()
     assert X.tuning_entries() == []
