@@ -381,7 +381,11 @@ struct Vec<double> {
 __device__ __forceinline__ float4 ldv4(const float4* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldv4(const double2* p) { return __ldcg(p); }
 
-template <typename T>
+// kRev: the blocks walk the chunks from the end of the array back to its start.  The
+// stencil phase before it walks its tiles forward, so the chunks this phase takes first
+// are the ones the stencil phase wrote last, still in L2 (and the chunks it takes last
+// are the first the next stencil phase reads).
+template <typename T, bool kRev = false>
 __device__ __forceinline__ double update_flat(const CGDesc<T>& d, int bl, int G, T alpha,
                                               const T* __restrict__ pn, T sigma = T(1)) {
   const long long n = d.g.nodes();
@@ -405,7 +409,9 @@ __device__ __forceinline__ double update_flat(const CGDesc<T>& d, int bl, int G,
     r[o] = rv;
     acc += (double)(rv * rv);
   }
-  for (long long c0 = lead + (long long)bl * kChunk; c0 < n; c0 += (long long)G * kChunk) {
+  const long long nch = n > lead ? (n - lead + kChunk - 1) / kChunk : 0;
+  for (long long m = bl; m < nch; m += G) {
+    const long long c0 = lead + (kRev ? nch - 1 - m : m) * kChunk;
     const long long c1 = c0 + kChunk < n ? c0 + kChunk : n;
     T tacc = T(0);
     if (vec && c1 - c0 == kChunk) {
@@ -930,7 +936,7 @@ __device__ bool cg_team(const CGDesc<T>& d, int p, int bl, CGState* st, double* 
     // (every block busy, one short column each -- lower latency)
     acc = 0.0;
     if (d.g.nodes() >= (long long)G * kChunk) {
-      acc = update_flat<T>(d, bl, G, (T)alpha, pnew, sigma);
+      acc = update_flat<T, kTma>(d, bl, G, (T)alpha, pnew, sigma);
     } else {
       for (long long t = bl; t < total_tiles; t += G)
         acc += (double)update_tile<T>(d, t, (T)alpha, pnew, sigma);
