@@ -129,8 +129,10 @@ typedef struct {
                               (its grid barriers and tensor-copy completions): a wait that
                               runs out ends the launch with EXCMG_ERR_TIMEOUT; 0 = 20000 */
   int test_phantom_blocks; /* TEST ONLY, 0 otherwise: adds this many members that are never
-                              launched to the block team of each cooperative CG launch of
-                              levels above 2^19 nodes, so that its first grid barrier cannot
+                              launched to the block team of each streaming cooperative CG
+                              launch (float64 grids too large for the shared-memory engine,
+                              about 2^19 nodes and up; float32 inner solves of MIXED), so
+                              that its first grid barrier cannot
                               complete and its wait must run out (with a short
                               wait_timeout_ms, to check that the call returns
                               EXCMG_ERR_TIMEOUT and the context stays usable) */

@@ -555,6 +555,9 @@ struct RingPhases {
 };
 
 // Origin of tile lt of the tensor-copy engine's tiling (tiles of kTX x kTileY columns).
+// The tiles cover nodes 0 .. n - 1 per direction: the far boundary faces (index n, and
+// the padding columns) are never written by the engine; p and q hold zeros there from
+// k_zero_far_faces, and the stencil reads them as halo.
 __device__ __forceinline__ TileXYZ tma_tile_coords(const Grid3& g, const Tiling& tl, long long lt) {
   TileXYZ c;
   const int bx = (int)(lt % tl.ntx);
@@ -564,7 +567,7 @@ __device__ __forceinline__ TileXYZ tma_tile_coords(const Grid3& g, const Tiling&
   c.x0 = bx * kTX;
   c.y0 = by * kTileY;
   c.z0 = bz * tl.tz;
-  c.z1 = min(c.z0 + tl.tz, g.nz + 1);
+  c.z1 = min(c.z0 + tl.tz, g.nz);
   return c;
 }
 
@@ -1281,40 +1284,59 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
 }
 
 // MIXED refinement: u += e / scale (the float32 correction of the scaled system), then
-// e = 0 for the next inner solve.  e has the padded float32 layout, u the float64 one;
-// a warp walks one row (j, k) at a time, lanes along x, four elements in flight each.
+// e = 0 for the next inner solve.  e has the padded float32 layout, u the unpadded
+// float64 one, whose nodes are one contiguous run: the threads stride through u's flat
+// index m (eight elements in flight each, consecutive lanes on consecutive nodes), and
+// e's index is m plus the padding of the rows before it, m / (nx + 1) found by a
+// multiply-high with the rounded-up reciprocal 2^64 / (nx + 1) (exact for m < 2^32 and
+// far beyond).  No row is split into a short last pass.
 __global__ void __launch_bounds__(kThreads)
     k_add_correction(int nprob, const CGDesc<float>* __restrict__ descs) {
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * kThreads) >> 5;
+  constexpr int kU = 8;
+  const unsigned long long tid = (unsigned long long)blockIdx.x * kThreads + threadIdx.x;
+  const unsigned long long nth = (unsigned long long)gridDim.x * kThreads;
   for (int p = 0; p < nprob; ++p) {
     const CGDesc<float>& d = descs[p];
     const Grid3 g = d.g;
-    const long long rows = (long long)(g.ny + 1) * (g.nz + 1);
+    const unsigned long long n1 = (unsigned long long)g.nx + 1;
+    const unsigned long long rows = (unsigned long long)(g.ny + 1) * (g.nz + 1);
     const double inv = 1.0 / d.scale;
     float* __restrict__ e = d.x;
     double* __restrict__ u = d.aux;
-    for (long long row = warp; row < rows; row += nwarps) {
-      const long long j = row % (g.ny + 1), k = row / (g.ny + 1);
-      float* er = e + j * g.sy + k * g.sz;
-      double* ur = u + j * d.aux_sy + k * d.aux_sz;
-      for (int i0 = 0; i0 <= g.nx; i0 += 4 * 32) {
-        float ev[4];
-        double uv[4];
+    if (d.aux_sy == (long long)n1 && d.aux_sz == (long long)(n1 * (g.ny + 1))) {
+      const unsigned long long n = n1 * rows;
+      const unsigned long long M = ~0ULL / n1 + 1;  // ceil(2^64 / n1); 2^64 / n1 if a power of 2
+      const unsigned long long pad = (unsigned long long)g.sy - n1;
+      for (unsigned long long m0 = tid; m0 < n; m0 += kU * nth) {
+        float ev[kU];
+        double uv[kU];
+        unsigned long long oe[kU];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int i = i0 + m * 32 + lane;
-          ev[m] = i <= g.nx ? __ldcs(er + i) : 0.f;
-          uv[m] = i <= g.nx ? __ldcs(ur + i) : 0.0;
+        for (int k = 0; k < kU; ++k) {
+          const unsigned long long m = m0 + k * nth;
+          oe[k] = m + __umul64hi(m, M) * pad;
+          ev[k] = m < n ? __ldcs(e + oe[k]) : 0.f;
+          uv[k] = m < n ? __ldcs(u + m) : 0.0;
         }
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int i = i0 + m * 32 + lane;
-          if (i <= g.nx) {
-            __stcs(ur + i, fma((double)ev[m], inv, uv[m]));
-            __stcs(er + i, 0.f);
+        for (int k = 0; k < kU; ++k) {
+          const unsigned long long m = m0 + k * nth;
+          if (m < n) {
+            __stcs(u + m, fma((double)ev[k], inv, uv[k]));
+            __stcs(e + oe[k], 0.f);
           }
+        }
+      }
+    } else {
+      // u with other strides: a warp per row (j, k), lanes along x
+      const int lane = threadIdx.x & 31;
+      for (unsigned long long row = tid >> 5; row < rows; row += nth >> 5) {
+        const long long j = (long long)(row % (g.ny + 1)), k = (long long)(row / (g.ny + 1));
+        float* er = e + j * g.sy + k * g.sz;
+        double* ur = u + j * d.aux_sy + k * d.aux_sz;
+        for (int i = lane; i <= g.nx; i += 32) {
+          ur[i] = fma((double)er[i], inv, ur[i]);
+          er[i] = 0.f;
         }
       }
     }
@@ -1416,9 +1438,11 @@ Tiling make_tma_tiling(const Grid3& g, int tz) {
   if (tz < 1) tz = 1;
   Tiling t;
   t.tz = tz;
-  t.ntx = (g.nx + 1 + kTX - 1) / kTX;
-  t.nty = (g.ny + 1 + kTileY - 1) / kTileY;
-  t.ntz = (g.nz + 1 + tz - 1) / tz;
+  // nodes 0 .. n - 1 per direction (see tma_tile_coords): whole tiles on power-of-two
+  // grids
+  t.ntx = (g.nx + kTX - 1) / kTX;
+  t.nty = (g.ny + kTileY - 1) / kTileY;
+  t.ntz = (g.nz + tz - 1) / tz;
   return t;
 }
 
@@ -1513,6 +1537,41 @@ cudaError_t launch_residual(bool out_float, int nprob, const ResDesc* descs, lon
     k_residual<float><<<grid, kThreads, 0, s>>>(nprob, descs, total_tiles, st, partials, counters);
   else
     k_residual<double><<<grid, kThreads, 0, s>>>(nprob, descs, total_tiles, st, partials, counters);
+  return cudaGetLastError();
+}
+
+// Zeros of p_a, p_b and q on the far boundary faces of a padded float32 grid: the
+// columns nx .. sy - 1 of every row, the row ny and the plane nz.  The tensor-copy CG
+// engine never writes these nodes (its tiles end at n - 1) and reads them as halo.
+__global__ void k_zero_far_faces(Grid3 g, float* a, float* b, float* c) {
+  const long long rows = (long long)(g.ny + 1) * (g.nz + 1);
+  const int cx = g.sy - g.nx;  // columns nx .. sy - 1
+  const long long n1 = rows * cx, n2 = (long long)g.sy * (g.nz + 1), n3 = (long long)g.sy * (g.ny + 1);
+  const long long n = n1 + n2 + n3;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long o;
+    if (t < n1) {
+      const long long row = t / cx;
+      o = (long long)(g.nx + (int)(t % cx)) + (row % (g.ny + 1)) * g.sy + (row / (g.ny + 1)) * g.sz;
+    } else if (t < n1 + n2) {
+      const long long u = t - n1;
+      o = (u % g.sy) + (long long)g.ny * g.sy + (u / g.sy) * g.sz;
+    } else {
+      const long long u = t - n1 - n2;
+      o = (u % g.sy) + (u / g.sy) * g.sy + (long long)g.nz * g.sz;
+    }
+    a[o] = 0.f;
+    b[o] = 0.f;
+    c[o] = 0.f;
+  }
+}
+
+cudaError_t launch_zero_far_faces(const CGDesc<float>& d, cudaStream_t s) {
+  const long long n = (long long)(d.g.ny + 1) * (d.g.nz + 1) * (d.g.sy - d.g.nx) +
+                      (long long)d.g.sy * (d.g.nz + d.g.ny + 2);
+  const long long blocks = std::min<long long>((n + kThreads - 1) / kThreads, 4096);
+  k_zero_far_faces<<<(int)std::max<long long>(blocks, 1), kThreads, 0, s>>>(d.g, d.pa, d.pb, d.q);
   return cudaGetLastError();
 }
 

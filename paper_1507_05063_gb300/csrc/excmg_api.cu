@@ -804,8 +804,10 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     }
     return EXCMG_OK;
   }
-  for (auto& it : items)
+  for (auto& it : items) {
     CK(cudaMemsetAsync(it.d32.x, 0, sizeof(float) * it.d32.g.nodes(), c.s));
+    CK(launch_zero_far_faces(it.d32, c.s));
+  }
   std::vector<int> cur(n);
   for (int a = 0; a < n; ++a) cur[a] = a;
   for (int pass = 0;; ++pass) {

@@ -180,6 +180,9 @@ cudaError_t launch_cg_step(int nprob, const CGDesc<T>* descs, long long total_ti
 cudaError_t launch_residual(bool out_float, int nprob, const ResDesc* descs,
                             long long total_tiles, int grid, CGState* st, double* partials,
                             unsigned* counters, cudaStream_t s);
+// Zeros p_a, p_b and q of one float32 problem on its far boundary faces (x = nx and the
+// padding columns, y = ny, z = nz), which the tensor-copy engine reads but never writes.
+cudaError_t launch_zero_far_faces(const CGDesc<float>& d, cudaStream_t s);
 cudaError_t launch_add_correction(int nprob, const CGDesc<float>* inner, long long total_tiles,
                                   int grid, cudaStream_t s);
 // MIXED: r *= scale on every problem's float32 residual, and the CG state's r.r and
@@ -231,7 +234,7 @@ bool encode_plane_map(CUtensorMap* m, float* base, const Grid3& g32);
 // All CG steps of ONE float64 grid of up to kResidentMaxNodes nodes in a cooperative
 // grid whose blocks keep the level's vectors in shared memory (resident_cg.cu).
 #ifndef EXCMG_RESIDENT_MAX_NODES
-#define EXCMG_RESIDENT_MAX_NODES (1 << 19)
+#define EXCMG_RESIDENT_MAX_NODES (1 << 20)
 #endif
 constexpr long long kResidentMaxNodes = EXCMG_RESIDENT_MAX_NODES;
 struct ResidentDesc {

@@ -3,8 +3,10 @@
 excmg_cg (and every level of excmg_solve) runs a float64 grid's CG steps on one of:
   * k_cg_cluster   -- up to 2,000 nodes (and the small grids of batched solves, up to
                       20,000), one thread-block cluster of 1-16 CTAs;
-  * k_cg_resident  -- 2,000 to 2^19 nodes, a cooperative grid with the vectors in shared
-                      memory (3D boxes, partial boxes at the far faces);
+  * k_cg_resident  -- from 2,000 nodes up to the largest grid whose boxes fit the shared
+                      memory of the co-resident blocks (about 730,000 interior nodes on
+                      GB300, never above 2^20), a cooperative grid with the vectors in
+                      shared memory (3D boxes, partial boxes at the far faces);
   * k_cg_persistent -- larger grids, streaming from HBM.
 The first two use the single-reduction recurrence (same iterates as the oracle's standard
 recurrence in exact arithmetic), so the GPU and the oracle run the same number of steps
@@ -57,7 +59,8 @@ ENGINE_CASES = [
     ((64, 32, 16), (1.0, 1.0, 1.0), "cg_resident_f64", 20),   # 36,465
     ((50, 36, 22), (1.0, 0.9, 0.6), "cg_resident_f64", 20),   # 43,401: partial boxes
     ((128, 64, 32), (1.0, 1.0, 1.0), "cg_resident_f64", 12),  # 276,705
-    ((160, 80, 40), (2.0, 1.0, 0.5), "cg_f64", 8),            # 534,681: streaming kernel
+    ((160, 80, 40), (2.0, 1.0, 0.5), "cg_resident_f64", 8),   # 534,681: largest boxes
+    ((208, 104, 52), (2.0, 1.0, 0.5), "cg_f64", 8),           # 1,163,085: streaming kernel
 ]
 
 

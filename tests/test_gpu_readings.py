@@ -134,7 +134,7 @@ def test_grid_barrier_wait_runs_out(X, precision):
     arrives; with a 5 ms bound the kernel gives up, the call returns EXCMG_ERR_TIMEOUT,
     and the context stays usable: the same call without the phantom then solves."""
     import time
-    N, L = (128, 64, 64), (1.0, 1.0, 1.0)  # 545,545 nodes: the cooperative engines
+    N, L = (256, 128, 64), (1.0, 1.0, 1.0)  # 2.1 M nodes: the streaming cooperative engines
     f, g, _ = P.make_inputs(P.PROBLEMS["exp3"], N)
     u0 = g.copy()
     u0[1:-1, 1:-1, 1:-1] = 0.0  # far from the solution: CG steps are needed
