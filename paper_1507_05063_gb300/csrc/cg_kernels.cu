@@ -1106,8 +1106,10 @@ __device__ double perim_lift(const double* __restrict__ u, const Grid3& g, const
 
 // Twice the right-hand side of eq. (compact) at interior node (i, j, k): 6 f_c + the 6
 // face values of f (the face values are re-read through L1 by the neighbouring threads),
-// or -2 b when b is given directly.  o is the node's offset.
+// or the value an earlier pass kept, or -2 b when b is given directly.  o is the node's
+// offset.
 __device__ __forceinline__ double res_rhs2(const ResDesc& d, int i, int j, int k, long long o) {
+  if (d.rhs2 != nullptr) return d.rhs2[o];
   if (d.src != nullptr) return -2.0 * d.src[o];
   const View& F = d.f;
   return fma(6.0, F.at(i, j, k), ((F.at(i - 1, j, k) + F.at(i + 1, j, k)) +
@@ -1226,10 +1228,10 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
           const long long o = i + j * g.sy + (long long)kc * g.sz;
           double rv = 0.0;
           if (colx && j > 0 && j < g.ny && kc > 0 && kc < g.nz) {
-            // twice the right-hand side; the factor 1/2 is applied inside the fused
-            // multiply-adds below, exactly
+            // twice the right-hand side (kept as it is for the later passes); the factor
+            // 1/2 is applied inside the fused multiply-add below, exactly
             const double rhs2 = res_rhs2(d, i, j, kc, o);
-            if (d.rhs_out) d.rhs_out[o] = -0.5 * rhs2;
+            if (d.rhs_out) d.rhs_out[o] = rhs2;
             // LHS(u) - RHS = -(A-stencil of u over all 19 nodes) - RHS
             rv = fma(-0.5, rhs2, -((Cm1[q] + Tm2[q]) + Tk));
             acc_r = fma(rv, rv, acc_r);

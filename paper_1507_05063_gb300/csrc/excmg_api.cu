@@ -223,7 +223,7 @@ struct ProbLayout {
   size_t coarse_off[EXCMG_MAX_LEVELS];  // u of levels 0 .. L-2 (float64)
   size_t r, pa, pb, q;                  // float64 CG vectors (finest size)
   size_t r32, pa32, pb32, q32, e32;     // float32 CG vectors (MIXED)
-  size_t rhs64;                         // MIXED: -RHS(f) of the level being refined
+  size_t rhs64;                         // MIXED: 2 RHS(f) of the level being refined
   size_t s0, s1;                        // resident CG: s by step parity (its grids' size)
   size_t bytes;
 };
@@ -659,7 +659,7 @@ struct Item {
   ResDesc res;
   CGDesc<double> d64;
   CGDesc<float> d32;
-  double* rhs_cache;    // MIXED: -RHS(f) kept between refinement residuals (NULL: none)
+  double* rhs_cache;    // MIXED: 2 RHS(f) kept between refinement residuals (NULL: none)
   double eps;           // stop at ||r|| <= eps ||b||
   long long nodes;
   // results
@@ -819,9 +819,9 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
       rt += r.t.count();
       if (items[a].rhs_cache && !r.src) {
         if (pass == 0) {
-          r.rhs_out = items[a].rhs_cache;  // keep -RHS(f) for the later passes
+          r.rhs_out = items[a].rhs_cache;  // keep 2 RHS(f) for the later passes
         } else {
-          r.src = items[a].rhs_cache;      // r = LHS(u) - RHS(f) without recomputing RHS
+          r.rhs2 = items[a].rhs_cache;     // r = LHS(u) - RHS(f) without recomputing RHS
           r.want_b = 0;                    // ||b|| is already in the state
         }
       }

@@ -151,9 +151,10 @@ struct ResDesc {
   const double* u;      // level solution, boundary = g
   View f;               // f at this level's nodes (unused when src is set)
   const double* src;    // NULL, or b given directly on interior nodes: r = LHS(u) + src
-                        // (the adjoint's A lambda = s with lambda's boundary zero; MIXED
-                        // refinement steps after the first reuse -RHS(f) from rhs_out)
-  double* rhs_out;      // NULL, or receives -RHS(f) on interior nodes (f path only)
+                        // (the adjoint's A lambda = s with lambda's boundary zero)
+  const double* rhs2;   // NULL, or 2 RHS(f) on interior nodes as an earlier pass kept it
+                        // in rhs_out (MIXED refinement steps after the first)
+  double* rhs_out;      // NULL, or receives 2 RHS(f) on interior nodes (f path only)
   void* r;              // TR* output
   long long osy, osz;   // node strides of r (the padded layout when TR is float; the
                         // padding columns nx + 1 .. osy - 1 are written as zeros)
