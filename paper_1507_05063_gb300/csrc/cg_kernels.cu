@@ -1057,7 +1057,9 @@ __global__ void __launch_bounds__(kThreads, kTma ? EXCMG_PERSIST_TMA_MIN_BLOCKS 
 // K3: r = LHS(u) - RHS(f) = b - A u_I (float64), sums r.r and b.b, CG state init
 // ---------------------------------------------------------------------------------
 #ifndef EXCMG_RES_MINB
-#define EXCMG_RES_MINB 3  // 24 warps per SM: measured faster than 16
+// 16 warps per SM, 128 registers: four rows per thread share the W + E sums of their
+// neighbourhood (2 row sums per node instead of 3); at 80 registers (24 warps) they spill
+#define EXCMG_RES_MINB 2
 #endif
 
 // A residual tile: kTX columns along x (one warp) x kTY * kResRows rows along y (each
@@ -1567,6 +1569,18 @@ __global__ void k_zero_far_faces(Grid3 g, float* a, float* b, float* c) {
     b[o] = 0.f;
     c[o] = 0.f;
   }
+}
+
+__global__ void k_export_states(const unsigned* __restrict__ src, unsigned* dst, int words) {
+  for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+}
+
+cudaError_t launch_export_states(const CGState* src, CGState* dst, int n, cudaStream_t s) {
+  static_assert(sizeof(CGState) % sizeof(unsigned) == 0, "CGState is copied in 32-bit words");
+  const int words = (int)(sizeof(CGState) / sizeof(unsigned)) * n;
+  k_export_states<<<1, kThreads, 0, s>>>(reinterpret_cast<const unsigned*>(src),
+                                         reinterpret_cast<unsigned*>(dst), words);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_zero_far_faces(const CGDesc<float>& d, cudaStream_t s) {

@@ -20,7 +20,7 @@ constexpr int kThreads = 256;    // threads of every tiled kernel
 constexpr int kTX = 32;          // x-width of a stencil tile (one warp)
 constexpr int kTY = 8;           // y-rows of a stencil tile
 #ifndef EXCMG_RES_ROWS
-#define EXCMG_RES_ROWS 1  // 2 and 4 measured slower
+#define EXCMG_RES_ROWS 4  // with 2 blocks per SM: 7% faster than 1 row at 3 blocks
 #endif
 constexpr int kResRows = EXCMG_RES_ROWS;  // y-rows per thread of the residual kernel
 constexpr int kMaxGrid = 4096;   // cap on persistent grid size (partials per problem)
@@ -181,6 +181,9 @@ cudaError_t launch_cg_step(int nprob, const CGDesc<T>* descs, long long total_ti
 cudaError_t launch_residual(bool out_float, int nprob, const ResDesc* descs,
                             long long total_tiles, int grid, CGState* st, double* partials,
                             unsigned* counters, cudaStream_t s);
+// Copies n CG states into a device-mapped page-locked host buffer (dst: its device
+// address), by one block: the states reach the host without a copy-engine transfer.
+cudaError_t launch_export_states(const CGState* src, CGState* dst, int n, cudaStream_t s);
 // Zeros p_a, p_b and q of one float32 problem on its far boundary faces (x = nx and the
 // padding columns, y = ny, z = nz), which the tensor-copy engine reads but never writes.
 cudaError_t launch_zero_far_faces(const CGDesc<float>& d, cudaStream_t s);
