@@ -142,6 +142,12 @@ typedef struct {
                               the process) lacks, and keep the fastest; 0 (default) = use the
                               cache where it holds the level, the models elsewhere; -1 = the
                               models only.  options.tile_z > 0 overrides both */
+  int res_rows;            /* y-rows per thread of the residual kernel: 0 (default) = the
+                              tuning cache's or the model's choice per level (the model:
+                              4 on grids of 2^26 nodes and more, else 1), 1 or 4 = that for
+                              every level; other values are EXCMG_ERR_INVALID_ARG.  Four
+                              rows share neighbour sums (fewer float64 instructions per
+                              node) at a lower occupancy. */
 } excmg_options;
 
 /* One entry of the launch-shape cache (options.autotune): a level grid and engine class
@@ -153,6 +159,8 @@ typedef struct {
   double res_ms, res_ms_model;  /* one residual launch at each (ms) */
   int cg_tz, cg_tz_model;       /* slab depth of its CG engine (0: the engine is not tiled) */
   double cg_ms, cg_ms_model;    /* one CG step at each (ms) */
+  int res_rows, res_rows_model; /* y-rows per thread of its residual launch (1 or 4); res_ms
+                                   is at (res_rows, res_tz), res_ms_model at the model's */
 } excmg_tuning;
 
 /* Copies up to `max` cache entries to out (NULL: none) and returns how many there are. */
@@ -219,7 +227,7 @@ typedef struct {
    inner_tol 1e-4, max_refine 50, fixed_iters NULL, tile_z 0, chunk 0,
    mixed_min_nodes 0, profile 0, dsolve DIRECT, eps_ratio 1 (uniform tolerance),
    prolong QUARTIC, history NULL, history_len 0, rhs_norm LIFT, wait_timeout_ms 0
-   (20 s), test_phantom_blocks 0, autotune 0. */
+   (20 s), test_phantom_blocks 0, autotune 0, res_rows 0. */
 void excmg_default_options(excmg_options* opt);
 
 /* Human-readable name of a status code (static string). */

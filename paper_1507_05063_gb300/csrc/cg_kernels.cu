@@ -1057,15 +1057,19 @@ __global__ void __launch_bounds__(kThreads, kTma ? EXCMG_PERSIST_TMA_MIN_BLOCKS 
 // K3: r = LHS(u) - RHS(f) = b - A u_I (float64), sums r.r and b.b, CG state init
 // ---------------------------------------------------------------------------------
 #ifndef EXCMG_RES_MINB
-// 16 warps per SM, 128 registers: four rows per thread share the W + E sums of their
-// neighbourhood (2 row sums per node instead of 3); at 80 registers (24 warps) they spill
-#define EXCMG_RES_MINB 2
+#define EXCMG_RES_MINB 3  // one row per thread: 24 warps per SM, measured faster than 16
+#endif
+#ifndef EXCMG_RES_MINB_WIDE
+// four rows per thread share the W + E sums of their neighbourhood (2 row sums per node
+// instead of 3) and need 128 registers: 16 warps per SM (at 80 registers they spill)
+#define EXCMG_RES_MINB_WIDE 2
 #endif
 
-// A residual tile: kTX columns along x (one warp) x kTY * kResRows rows along y (each
-// thread takes kResRows adjacent rows) x tz planes, covering nodes 0 .. n per direction.
+// A residual tile: kTX columns along x (one warp) x kTY * R rows along y (each thread
+// takes R adjacent rows) x tz planes, covering nodes 0 .. n per direction.
 // (Tiles of the interior nodes 1 .. n, with the index-0 boundary nodes written by their
 // neighbours, hold no padding for power-of-two grids but measured 40% slower.)
+template <int R>
 __device__ __forceinline__ TileXYZ res_tile_coords(const Grid3& g, const Tiling& tl, long long lt) {
   TileXYZ c;
   const int bx = (int)(lt % tl.ntx);
@@ -1073,7 +1077,7 @@ __device__ __forceinline__ TileXYZ res_tile_coords(const Grid3& g, const Tiling&
   const int by = (int)(r % tl.nty);
   const int bz = (int)(r / tl.nty);
   c.x0 = bx * kTX;
-  c.y0 = by * kTY * kResRows;
+  c.y0 = by * kTY * R;
   c.z0 = bz * tl.tz;
   c.z1 = min(c.z0 + tl.tz, g.nz + 1);
   return c;
@@ -1133,8 +1137,8 @@ __device__ __noinline__ void residual_flush(double acc_r, double acc_b, double a
   }
 }
 
-// Each thread marches its kResRows rows of one x-column through the tile's planes.  Per
-// plane it loads the (kResRows + 2) x 3 neighbourhood (through the read-only cache:
+// Each thread marches its R rows of one x-column through the tile's planes.  Per
+// plane it loads the (R + 2) x 3 neighbourhood (through the read-only cache:
 // neighbouring threads share the lines; no staging, no block barrier) and forms, per row,
 // the in-plane part C = c0 P + fx S_x + fy S_y + exy E_xy and the out-of-plane part
 // T = fz P + exz S_x + eyz S_y of the 19-point sum, with S_x = W + E computed once per
@@ -1146,11 +1150,10 @@ __device__ __noinline__ void residual_flush(double acc_r, double acc_b, double a
 // Next to an x boundary face only one lane of the warp is such a node: those nodes are
 // left out of the plane loop and formed after it, one lane per plane, so a warp issues
 // the lift once for up to 32 planes instead of once per plane for one lane.
-template <typename TR>
-__global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
+template <typename TR, int R>
+__global__ void __launch_bounds__(kThreads, R > 1 ? EXCMG_RES_MINB_WIDE : EXCMG_RES_MINB)
     k_residual(int nprob, const ResDesc* __restrict__ descs, long long total_tiles,
                CGState* st, double* partials, unsigned* counters) {
-  constexpr int R = kResRows;
   static_assert(kTX == 32, "one warp per x-run of a residual tile row");
   __shared__ int s_active[kMaxProb];
   __shared__ double s_part[3 * kMaxProb];
@@ -1182,7 +1185,7 @@ __global__ void __launch_bounds__(kThreads, EXCMG_RES_MINB)
     TR* __restrict__ rout = reinterpret_cast<TR*>(d.r);
     // output strides: the padded float32 layout, or the grid's own for float64
     const long long osy = sizeof(TR) == 4 ? d.osy : g.sy, osz = sizeof(TR) == 4 ? d.osz : g.sz;
-    const TileXYZ c = res_tile_coords(g, d.t, t - d.tile_begin);
+    const TileXYZ c = res_tile_coords<R>(g, d.t, t - d.tile_begin);
     const int i = c.x0 + tx, jb = c.y0 + R * ty;  // rows jb .. jb + R - 1
     if (c.x0 >= g.nx || c.y0 >= g.ny || c.z0 >= g.nz) {
       // a tile of boundary nodes only (the last column, row or plane of the grid and the
@@ -1498,21 +1501,25 @@ int persistent_grid(long long total_tiles) {
   return g < 1 ? 1 : (int)g;
 }
 
-static int g_res_grid = 0;
+static int g_res_grid[2] = {0, 0};
 
-int residual_grid(long long total_tiles) {
-  if (g_res_grid == 0) {
+int residual_grid(long long total_tiles, int rows) {
+  const int w = rows > 1 ? 1 : 0;
+  if (g_res_grid[w] == 0) {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual<double>, kThreads, 0);
+    if (w)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual<double, kResRowsWide>, kThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual<double, 1>, kThreads, 0);
     if (sms <= 0) sms = 1;
     if (occ <= 0) occ = 1;
-    g_res_grid = sms * occ;
+    g_res_grid[w] = sms * occ;
     // the residual publishes 3 partials per block into room for 2 x kMaxGrid
-    if (g_res_grid > 2 * kMaxGrid / 3) g_res_grid = 2 * kMaxGrid / 3;
+    if (g_res_grid[w] > 2 * kMaxGrid / 3) g_res_grid[w] = 2 * kMaxGrid / 3;
   }
-  long long g = total_tiles < g_res_grid ? total_tiles : g_res_grid;
+  long long g = total_tiles < g_res_grid[w] ? total_tiles : g_res_grid[w];
   return g < 1 ? 1 : (int)g;
 }
 
@@ -1536,11 +1543,16 @@ template cudaError_t launch_cg_step<float>(int, const CGDesc<float>*, long long,
 
 cudaError_t launch_residual(bool out_float, int nprob, const ResDesc* descs, long long total_tiles,
                             int grid, CGState* st, double* partials, unsigned* counters,
-                            cudaStream_t s) {
-  if (out_float)
-    k_residual<float><<<grid, kThreads, 0, s>>>(nprob, descs, total_tiles, st, partials, counters);
+                            cudaStream_t s, int rows) {
+  if (rows != 1 && rows != kResRowsWide) return cudaErrorInvalidValue;
+  if (out_float && rows > 1)
+    k_residual<float, kResRowsWide><<<grid, kThreads, 0, s>>>(nprob, descs, total_tiles, st, partials, counters);
+  else if (out_float)
+    k_residual<float, 1><<<grid, kThreads, 0, s>>>(nprob, descs, total_tiles, st, partials, counters);
+  else if (rows > 1)
+    k_residual<double, kResRowsWide><<<grid, kThreads, 0, s>>>(nprob, descs, total_tiles, st, partials, counters);
   else
-    k_residual<double><<<grid, kThreads, 0, s>>>(nprob, descs, total_tiles, st, partials, counters);
+    k_residual<double, 1><<<grid, kThreads, 0, s>>>(nprob, descs, total_tiles, st, partials, counters);
   return cudaGetLastError();
 }
 

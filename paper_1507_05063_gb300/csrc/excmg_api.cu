@@ -62,14 +62,14 @@ Tiling make_tiling(const Grid3& g, int tz) {
 // Tiles of boundary nodes only cost nothing (k_residual writes zeros there), and every
 // block of a round waits for the slowest, so a deep slab that leaves blocks idle loses
 // to a thin one that fills every block.
-int choose_res_tz(const Grid3& g, int grid_blocks, int requested) {
+int choose_res_tz(const Grid3& g, int grid_blocks, int requested, int rows) {
   if (requested > 0) return requested;
   int best = 16;
   double best_cost = 1e300;
   const int cands[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64};
   for (int tz : cands) {
     const long long tiles = (long long)((g.nx + kTX - 1) / kTX) *
-                            ((g.ny + kTY * kResRows - 1) / (kTY * kResRows)) * ((g.nz + tz - 1) / tz);
+                            ((g.ny + kTY * rows - 1) / (kTY * rows)) * ((g.nz + tz - 1) / tz);
     const long long rounds = (tiles + grid_blocks - 1) / grid_blocks;
     const double cost = (double)rounds * (std::min(tz, g.nz + 1) + 2);
     if (cost < best_cost - 1e-9) {
@@ -80,11 +80,13 @@ int choose_res_tz(const Grid3& g, int grid_blocks, int requested) {
   return best;
 }
 
-Tiling make_res_tiling(const Grid3& g, int tz) {
+Tiling make_res_tiling(const Grid3& g, int tz, int rows) {
   Tiling t = make_tiling(g, tz);
-  t.nty = (g.ny + 1 + kTY * kResRows - 1) / (kTY * kResRows);
+  t.nty = (g.ny + 1 + kTY * rows - 1) / (kTY * rows);
   return t;
 }
+
+int res_rows_model(const Grid3& g) { return g.nodes() >= kResWideMinNodes ? kResRowsWide : 1; }
 
 
 // Slab depth: among 1..64 the one minimising (waves of tiles) x (planes staged per tile),
@@ -172,6 +174,7 @@ bool options_ok(const excmg_options* o) {
     return false;
   if (o->test_phantom_blocks < 0 || o->test_phantom_blocks > 64) return false;
   if (o->autotune < -1 || o->autotune > 1) return false;
+  if (o->res_rows != 0 && o->res_rows != 1 && o->res_rows != kResRowsWide) return false;
   return true;
 }
 
@@ -706,12 +709,13 @@ struct Item {
 };
 
 ResDesc make_res(const Grid3& g, int tile_z, int slot, const double* x, View f,
-                 const double* src) {
+                 const double* src, int rows) {
   ResDesc r;
   memset(&r, 0, sizeof(r));
   r.g = g;
   r.A = make_coef(g);
-  r.t = make_res_tiling(g, choose_res_tz(g, residual_grid(1LL << 40), tile_z));
+  r.rows = rows;
+  r.t = make_res_tiling(g, choose_res_tz(g, residual_grid(1LL << 40, rows), tile_z, rows), rows);
   r.slot = slot;
   r.u = x;
   r.f = f;
@@ -758,11 +762,19 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
   std::vector<CGState> hs;
   std::vector<ResDesc> hr;
   long long tiles = 0, rtiles = 0;  // CG tiles, residual tiles
+  // one residual launch serves every problem: they share its rows per thread (one
+  // row unless all of them take more)
+  int rows = kResRowsWide;
+  for (auto& it : items) rows = std::min(rows, it.res.rows);
   for (int a = 0; a < n; ++a) {
     Item& it = items[a];
     it.iters = it.refs = 0;
     it.status = EXCMG_OK;
     it.relres = 0.0;
+    if (it.res.rows != rows) {
+      it.res.t = make_res_tiling(it.res.g, it.res.t.tz, rows);
+      it.res.rows = rows;
+    }
     ResDesc r = it.res;
     r.tile_begin = rtiles;
     if (!it.d64.direct) rtiles += r.t.count();  // DSOLVE levels form their own b
@@ -809,8 +821,8 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     if (nres > 0) {
       CK(cudaMemcpyAsync(c.resd(), hr.data(), sizeof(ResDesc) * nres, cudaMemcpyHostToDevice, c.s));
       CK(c.timed(EXCMG_K_RESIDUAL, res_nodes, [&] {
-        return launch_residual(false, nres, c.resd(), rtiles, residual_grid(rtiles), c.st(), c.partials(),
-                               c.counters(), c.s);
+        return launch_residual(false, nres, c.resd(), rtiles, residual_grid(rtiles, rows), c.st(),
+                               c.partials(), c.counters(), c.s, rows);
       }));
     }
     // DSOLVE levels: one direct solve each (their states are done with 0 steps, so the
@@ -871,7 +883,8 @@ excmg_status solve_items_impl(const Ctx& c, std::vector<Item>& items, const excm
     for (int a : cur) rnodes += (double)items[a].nodes;
     CK(cudaMemcpyAsync(c.resd(), rr.data(), sizeof(ResDesc) * nr, cudaMemcpyHostToDevice, c.s));
     CK(c.timed(EXCMG_K_RESIDUAL, rnodes, [&] {
-      return launch_residual(true, nr, c.resd(), rt, residual_grid(rt), c.st(), c.partials(), c.counters(), c.s);
+      return launch_residual(true, nr, c.resd(), rt, residual_grid(rt, rows), c.st(), c.partials(),
+                             c.counters(), c.s, rows);
     }));
     excmg_status e = read_states(c, nslots, hs);
     if (e != EXCMG_OK) return e;
@@ -951,19 +964,23 @@ bool level_f32(const Grid3& g, bool dsolve_level, const excmg_options* o) {
 // Launch shapes of a level: the caller's tile_z, else the tuned ones (options.autotune
 // >= 0 and a cache entry), else the models.
 struct Shapes {
-  int res_tz, cg_tz, tma_tz;
+  int res_tz, cg_tz, tma_tz, res_rows;
 };
 Shapes level_shapes(const Grid3& g, bool dsolve_level, const excmg_options* o) {
   Shapes sh;
   const int tz = choose_tz(g, persistent_grid(1LL << 40), o->tile_z);
   sh.cg_tz = tz;
   sh.tma_tz = o->tile_z > 0 ? tz : tma_slab_depth(tz);
-  sh.res_tz = choose_res_tz(g, residual_grid(1LL << 40), o->tile_z);
+  sh.res_rows = o->res_rows > 0 ? o->res_rows : res_rows_model(g);
+  sh.res_tz = choose_res_tz(g, residual_grid(1LL << 40, sh.res_rows), o->tile_z, sh.res_rows);
   excmg_tuning t;
   if (o->tile_z == 0 && o->autotune >= 0 && tune_lookup(g, level_f32(g, dsolve_level, o), &t)) {
     // an entry's cg_tz is 0 where the single solve's engine for the grid is not tiled
     // (resident or cluster): the model's depth stays for the tiled engines of a batch
-    if (t.res_tz > 0) sh.res_tz = t.res_tz;
+    if (t.res_tz > 0 && (o->res_rows == 0 || o->res_rows == t.res_rows)) {
+      sh.res_tz = t.res_tz;
+      if (t.res_rows > 0) sh.res_rows = t.res_rows;
+    }
     if (t.cg_tz > 0) {
       if (level_f32(g, dsolve_level, o))
         sh.tma_tz = t.cg_tz;
@@ -984,7 +1001,7 @@ Item make_item(Prob& p, int l, int slot, const excmg_options* o) {
   const double ratio = o->eps_ratio > 0 ? o->eps_ratio : 1.0;
   it.eps = (l < 2) ? o->eps_coarse : o->eps * std::pow(ratio, (double)((int)p.lv.size() - 1 - l));
   it.nodes = g.nodes();
-  it.res = make_res(g, sh.res_tz, slot, p.level_u(l), p.fview(l), nullptr);
+  it.res = make_res(g, sh.res_tz, slot, p.level_u(l), p.fview(l), nullptr, sh.res_rows);
   it.res.forcing = o->rhs_norm == EXCMG_RHS_NORM_FORCING;
   CGDesc<double>& d = it.d64;
   d.g = g;
@@ -1049,11 +1066,12 @@ excmg_status tune_levels(Prob& p, const excmg_options* o, const Ctx& c0) {
     om.inner_tol = 1e-30;
     const Shapes model = level_shapes(g, false, &om);
     const bool cg_tiled = f32 || g.nodes() > kResidentMaxNodes;
-    // one run: residual + three CG steps at slab depth tz for both; returns the mean
-    // residual launch and the mean CG step (ms)
-    auto run = [&](int tz, double& res_ms, double& step_ms) -> excmg_status {
+    // one run: residual + three CG steps at slab depth tz for both, the residual with
+    // `rows` rows per thread; returns the mean residual launch and the mean CG step (ms)
+    auto run = [&](int tz, int rows, double& res_ms, double& step_ms) -> excmg_status {
       excmg_options ot = om;
       ot.tile_z = tz;
+      ot.res_rows = rows;
       Ctx c = c0;
       c.defer = false;
       c.hist = nullptr;
@@ -1087,6 +1105,7 @@ excmg_status tune_levels(Prob& p, const excmg_options* o, const Ctx& c0) {
     t.N[2] = g.nz;
     t.f32 = f32 ? 1 : 0;
     t.res_tz = t.res_tz_model = model.res_tz;
+    t.res_rows = t.res_rows_model = model.res_rows;
     t.cg_tz = t.cg_tz_model = cg_tiled ? (f32 ? model.tma_tz : model.cg_tz) : 0;
     double best_res = 1e300, best_cg = 1e300;
     std::vector<int> cands = {2, 4, 6, 8, 10, 12, 16, 20, 24, 32, 48};
@@ -1096,24 +1115,29 @@ excmg_status tune_levels(Prob& p, const excmg_options* o, const Ctx& c0) {
     cands.push_back(f32 ? model.tma_tz : model.cg_tz);
     std::sort(cands.begin(), cands.end());
     cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
-    for (int tz : cands) {
-      if (tz < 1 || tz > g.nz + 1) continue;
-      double rm = 0.0, sm = 0.0;
-      excmg_status e = run(tz, rm, sm);
-      if (e != EXCMG_OK) return e;
-      if (rm > 0 && rm < best_res) {
-        best_res = rm;
-        t.res_tz = tz;
-      }
-      if (tz == model.res_tz) t.res_ms_model = rm;
-      if (cg_tiled && sm > 0) {
-        if (sm < best_cg) {
-          best_cg = sm;
-          t.cg_tz = tz;
+    // the CG engine's depths are timed in the one-row runs; the residual's over both
+    // row counts
+    const int row_cands[] = {1, kResRowsWide};
+    for (int rows : row_cands)
+      for (int tz : cands) {
+        if (tz < 1 || tz > g.nz + 1) continue;
+        double rm = 0.0, sm = 0.0;
+        excmg_status e = run(tz, rows, rm, sm);
+        if (e != EXCMG_OK) return e;
+        if (rm > 0 && rm < best_res) {
+          best_res = rm;
+          t.res_tz = tz;
+          t.res_rows = rows;
         }
-        if (tz == t.cg_tz_model) t.cg_ms_model = sm;
+        if (tz == model.res_tz && rows == model.res_rows) t.res_ms_model = rm;
+        if (rows == 1 && cg_tiled && sm > 0) {
+          if (sm < best_cg) {
+            best_cg = sm;
+            t.cg_tz = tz;
+          }
+          if (tz == t.cg_tz_model) t.cg_ms_model = sm;
+        }
       }
-    }
     t.res_ms = best_res < 1e300 ? best_res : 0.0;
     t.cg_ms = best_cg < 1e300 ? best_cg : 0.0;
     if (t.res_ms_model == 0.0) t.res_ms_model = t.res_ms;
@@ -1344,6 +1368,7 @@ void excmg_default_options(excmg_options* o) {
   o->wait_timeout_ms = 0.0;
   o->test_phantom_blocks = 0;
   o->autotune = 0;
+  o->res_rows = 0;
 }
 
 int excmg_tuning_entries(excmg_tuning* out, int max) {
@@ -1593,12 +1618,13 @@ excmg_status excmg_residual(const excmg_grid* grid, const double* f, const doubl
   c.H = header_layout(1);
   c.s = static_cast<cudaStream_t>(stream);
   const Grid3 g = make_grid(grid->Nx, grid->Ny, grid->Nz, grid->Lx, grid->Ly, grid->Lz);
-  ResDesc d = make_res(g, 0, 0, u, View{f, 1, g.sy, g.sz}, nullptr);
+  const int rows = res_rows_model(g);
+  ResDesc d = make_res(g, 0, 0, u, View{f, 1, g.sy, g.sz}, nullptr, rows);
   d.r = r;
   CK(cudaMemsetAsync(c.counters(), 0, sizeof(unsigned), c.s));
   CK(cudaMemcpyAsync(c.resd(), &d, sizeof(d), cudaMemcpyHostToDevice, c.s));
-  CK(launch_residual(false, 1, c.resd(), d.t.count(), residual_grid(d.t.count()), c.st(),
-                     c.partials(), c.counters(), c.s));
+  CK(launch_residual(false, 1, c.resd(), d.t.count(), residual_grid(d.t.count(), rows), c.st(),
+                     c.partials(), c.counters(), c.s, rows));
   std::vector<CGState> hs;
   excmg_status e = read_states(c, 1, hs);
   if (e != EXCMG_OK) return e;

@@ -19,10 +19,15 @@ constexpr int kMaxProb = 128;    // problems per batched launch
 constexpr int kThreads = 256;    // threads of every tiled kernel
 constexpr int kTX = 32;          // x-width of a stencil tile (one warp)
 constexpr int kTY = 8;           // y-rows of a stencil tile
-#ifndef EXCMG_RES_ROWS
-#define EXCMG_RES_ROWS 4  // with 2 blocks per SM: 7% faster than 1 row at 3 blocks
+// y-rows per thread of the residual kernel: 1 or kResRowsWide, per launch (ResDesc.rows).
+// Four rows share their W + E sums (7% faster on 1024x512x512) but run 16 warps per SM
+// instead of 24 (17% slower on 512x256x128); the tuning cache decides per level grid,
+// else grids of at least EXCMG_RES_WIDE_MIN_NODES nodes take four.
+constexpr int kResRowsWide = 4;
+#ifndef EXCMG_RES_WIDE_MIN_NODES
+#define EXCMG_RES_WIDE_MIN_NODES (1LL << 26)
 #endif
-constexpr int kResRows = EXCMG_RES_ROWS;  // y-rows per thread of the residual kernel
+constexpr long long kResWideMinNodes = EXCMG_RES_WIDE_MIN_NODES;
 constexpr int kMaxGrid = 4096;   // cap on persistent grid size (partials per problem)
 #ifndef EXCMG_CLUSTER_MAX_NODES
 #define EXCMG_CLUSTER_MAX_NODES 20000
@@ -95,10 +100,12 @@ struct Tiling {
   __host__ __device__ long long count() const { return (long long)ntx * nty * ntz; }
 };
 Tiling make_tiling(const Grid3& g, int tz);
-// The residual kernel's tiling: kTY * kResRows rows per tile, the same x-width, slab
-// depth tz (choose_res_tz: the residual's own model of its launch).
-Tiling make_res_tiling(const Grid3& g, int tz);
-int choose_res_tz(const Grid3& g, int grid_blocks, int requested);
+// The residual kernel's tiling: kTY * rows rows per tile, the same x-width, slab depth tz
+// (choose_res_tz: the residual's own model of its launch).
+Tiling make_res_tiling(const Grid3& g, int tz, int rows);
+int choose_res_tz(const Grid3& g, int grid_blocks, int requested, int rows);
+// The model's rows per thread of the residual kernel for grid g (1 or kResRowsWide).
+int res_rows_model(const Grid3& g);
 int choose_tz(const Grid3& g, int grid_blocks, int requested);
 
 // Tensor maps of one float32 CG problem (cp.async.bulk.tensor): r and the two p buffers,
@@ -168,6 +175,8 @@ struct ResDesc {
   int fixed;            // exact iteration count
   double* hist;         // NULL, or receives r.r of the start in hist[0] (device)
   int hist_len;
+  int rows;             // y-rows per thread of the tiling t (1 or kResRowsWide); the same
+                        // for every problem of one launch
 };
 
 // Launch helpers (defined in cg_kernels.cu).  `descs` point to DEVICE copies.
@@ -180,7 +189,7 @@ cudaError_t launch_cg_step(int nprob, const CGDesc<T>* descs, long long total_ti
                            cudaEvent_t e2 = nullptr);
 cudaError_t launch_residual(bool out_float, int nprob, const ResDesc* descs,
                             long long total_tiles, int grid, CGState* st, double* partials,
-                            unsigned* counters, cudaStream_t s);
+                            unsigned* counters, cudaStream_t s, int rows);
 // Copies n CG states into a device-mapped page-locked host buffer (dst: its device
 // address), by one block: the states reach the host without a copy-engine transfer.
 cudaError_t launch_export_states(const CGState* src, CGState* dst, int n, cudaStream_t s);
@@ -195,7 +204,7 @@ cudaError_t launch_scale_rhs(int nprob, const CGDesc<float>* inner, long long to
                              int grid, CGState* st, cudaStream_t s);
 int persistent_grid(long long total_tiles);
 // Blocks of a residual launch: all co-resident blocks of k_residual, at most one per tile.
-int residual_grid(long long total_tiles);
+int residual_grid(long long total_tiles, int rows);
 
 // All CG steps of every problem of `descs` in one cooperative launch.  Problem p owns
 // the blocks [blk_begin, blk_begin + blk_count) and iterates independently of the

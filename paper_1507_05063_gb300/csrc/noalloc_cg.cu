@@ -120,7 +120,8 @@ extern "C" excmg_status excmg_cg_noalloc(const excmg_grid* grid, const double* f
   memset(&rd, 0, sizeof(rd));
   rd.g = g;
   rd.A = make_coef(g);
-  rd.t = make_res_tiling(g, choose_res_tz(g, residual_grid(1LL << 40), opt->tile_z));
+  rd.rows = 1;
+  rd.t = make_res_tiling(g, choose_res_tz(g, residual_grid(1LL << 40, 1), opt->tile_z, 1), 1);
   rd.slot = 0;
   rd.u = u;
   rd.f = View{f, 1, g.sy, g.sz};
@@ -151,8 +152,8 @@ extern "C" excmg_status excmg_cg_noalloc(const excmg_grid* grid, const double* f
   CKN(cudaMemcpyAsync(base + L.cgd, &cd, sizeof(cd), cudaMemcpyHostToDevice, s));
   const ResDesc* drd = reinterpret_cast<const ResDesc*>(base + L.resd);
   const CGDesc<double>* dcd = reinterpret_cast<const CGDesc<double>*>(base + L.cgd);
-  CKN(launch_residual(false, 1, drd, rd.t.count(), residual_grid(rd.t.count()), st, partials,
-                      counters, s));
+  CKN(launch_residual(false, 1, drd, rd.t.count(), residual_grid(rd.t.count(), 1), st, partials,
+                      counters, s, 1));
   long long launches = 1;
   CGState hs;
   int chunk = opt->chunk > 0 ? opt->chunk : 4;

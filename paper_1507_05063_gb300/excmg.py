@@ -50,14 +50,15 @@ class Options(ctypes.Structure):
                 ("prolong", ctypes.c_int), ("history", ctypes.POINTER(ctypes.c_double)),
                 ("history_len", ctypes.c_int), ("rhs_norm", ctypes.c_int),
                 ("wait_timeout_ms", ctypes.c_double), ("test_phantom_blocks", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("res_rows", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int * 3), ("f32", ctypes.c_int), ("res_tz", ctypes.c_int),
                 ("res_tz_model", ctypes.c_int), ("res_ms", ctypes.c_double),
                 ("res_ms_model", ctypes.c_double), ("cg_tz", ctypes.c_int), ("cg_tz_model", ctypes.c_int),
-                ("cg_ms", ctypes.c_double), ("cg_ms_model", ctypes.c_double)]
+                ("cg_ms", ctypes.c_double), ("cg_ms_model", ctypes.c_double),
+                ("res_rows", ctypes.c_int), ("res_rows_model", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -135,7 +136,8 @@ def tuning_entries():
     n = excmg_tuning_entries(arr, n)
     return [{"N": list(t.N), "f32": t.f32, "res_tz": t.res_tz, "res_tz_model": t.res_tz_model,
              "res_ms": t.res_ms, "res_ms_model": t.res_ms_model, "cg_tz": t.cg_tz,
-             "cg_tz_model": t.cg_tz_model, "cg_ms": t.cg_ms, "cg_ms_model": t.cg_ms_model}
+             "cg_tz_model": t.cg_tz_model, "cg_ms": t.cg_ms, "cg_ms_model": t.cg_ms_model,
+             "res_rows": t.res_rows, "res_rows_model": t.res_rows_model}
             for t in arr[:n]]
 
 
@@ -164,7 +166,7 @@ RHS_NORM = {"lift": 0, "forcing": 1}
 def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
                  inner_tol=1e-4, max_refine=50, fixed_iters=None, tile_z=0, chunk=0, profile=0,
                  mixed_min_nodes=0, dsolve="direct", eps_ratio=1.0, prolong="quartic", history=0,
-                 rhs_norm="lift", wait_timeout_ms=0.0, test_phantom_blocks=0, autotune=0):
+                 rhs_norm="lift", wait_timeout_ms=0.0, test_phantom_blocks=0, autotune=0, res_rows=0):
     o = Options()
     excmg_default_options(ctypes.byref(o))
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else int(precision)
@@ -184,6 +186,7 @@ def make_options(precision="fp64", eps=1e-9, eps_coarse=1e-12, max_iter=100000,
     o.wait_timeout_ms = float(wait_timeout_ms)
     o.test_phantom_blocks = int(test_phantom_blocks)
     o.autotune = int(autotune)
+    o.res_rows = int(res_rows)
     keep = {}
     if fixed_iters is not None:
         keep["fixed"] = (ctypes.c_int * len(fixed_iters))(*[int(v) for v in fixed_iters])

@@ -188,6 +188,7 @@ def test_autotune_fills_cache_and_keeps_the_solution(X):
         assert ents, prec
         for e in ents:
             assert e["res_tz"] >= 1 and e["res_ms"] > 0 and e["res_ms"] <= e["res_ms_model"] * 1.0001
+            assert e["res_rows"] in (1, 4) and e["res_rows_model"] in (1, 4)
             if e["cg_tz"]:
                 assert e["cg_ms"] > 0 and e["cg_ms"] <= e["cg_ms_model"] * 1.0001
         tuned = X.solve(fd, gd, L, N0, **kw)
@@ -207,3 +208,25 @@ def test_autotune_fills_cache_and_keeps_the_solution(X):
         assert np.max(np.abs(host(ub) - u)) == pytest.approx(np.max(np.abs(host(single["u"]) - u)), rel=1e-2)
     X.excmg_tuning_clear()
     assert X.tuning_entries() == []
+
+
+# ------------------------------------------------------------------ residual rows per thread
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_residual_rows_per_thread_agree(X, precision):
+    """options.res_rows: the residual kernel with one and with four rows per thread forms
+    every node's residual with the same grouping, so the two solves agree to rounding (the
+    block sums of r.r and b.b add in another order); both meet the tolerance."""
+    N, N0, L = (96, 80, 64), (6, 5, 4), (1.0, 0.9, 0.8)
+    f, g, u = P.make_inputs(P.PROBLEMS["exp3"], N, L)
+    fd, gd = dev(f), dev(g)
+    kw = dict(eps=1e-10, precision=precision, mixed_min_nodes=1 << 15, autotune=-1)
+    a = X.solve(fd, gd, L, N0, res_rows=1, **kw)
+    b = X.solve(fd, gd, L, N0, res_rows=4, **kw)
+    for r in (a, b):
+        assert all(x <= 1e-10 * 1.0000001 for x in r["stats"]["relres"][2:])
+    assert all(abs(x - y) <= 1 for x, y in zip(a["stats"]["iters"], b["stats"]["iters"]))
+    ea, eb = np.max(np.abs(host(a["u"]) - u)), np.max(np.abs(host(b["u"]) - u))
+    assert eb == pytest.approx(ea, rel=1e-2)
+    with pytest.raises(X.ExcmgError):
+        X.solve(fd, gd, L, N0, res_rows=2, **kw)
