@@ -217,7 +217,7 @@ def test_residual_rows_per_thread_agree(X, precision):
     """options.res_rows: the residual kernel with one and with four rows per thread forms
     every node's residual with the same grouping, so the two solves agree to rounding (the
     block sums of r.r and b.b add in another order); both meet the tolerance."""
-    N, N0, L = (96, 80, 64), (6, 5, 4), (1.0, 0.9, 0.8)
+    N, N0, L = (96, 64, 32), (6, 4, 2), (1.0, 0.9, 0.8)
     f, g, u = P.make_inputs(P.PROBLEMS["exp3"], N, L)
     fd, gd = dev(f), dev(g)
     kw = dict(eps=1e-10, precision=precision, mixed_min_nodes=1 << 15, autotune=-1)

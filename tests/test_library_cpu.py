@@ -58,7 +58,8 @@ def test_invalid_options_rejected(X):
     g = X.make_grid((1, 1, 1), (32, 32, 32), (4, 4, 4))
     for kw in ({"precision": 7}, {"eps": -1.0}, {"max_iter": -3}, {"precision": "mixed", "inner_tol": 2.0},
                {"mixed_min_nodes": -1}, {"eps_ratio": -1.0}, {"eps_ratio": float("nan")},
-               {"prolong": 7}, {"dsolve": 5}, {"precision": "mixed", "history": 8}):
+               {"prolong": 7}, {"dsolve": 5}, {"precision": "mixed", "history": 8},
+               {"res_rows": 2}, {"res_rows": -1}, {"autotune": 2}):
         o, _ = X.make_options(**kw)
         assert X.excmg_workspace_size(ctypes.byref(g), ctypes.byref(o)) == 0
 
