@@ -284,7 +284,10 @@ excmg_status excmg_grad(const excmg_grid* grid, const double* u, double* ux, dou
  * excmg_solve_batched -- `nprob` independent problems (each its own grid, f, g) solved by
  * Algorithm 1 together: each CG step of every active problem runs in ONE launch of the
  * stencil kernels over the union of all problems' tiles; problems are aligned on their
- * finest level.  grids[nprob]: host array; f, g, u: host arrays of device pointers.
+ * finest level.  Problems whose finest grid has 2^18 nodes or more run first, one after
+ * another, as single solves (each fills the GPU by itself and takes a single solve's CG
+ * engines); the others share the batch's launches.  The results are those of single
+ * solves up to rounding.  grids[nprob]: host array; f, g, u: host arrays of device pointers.
  * opt: shared options (fixed_iters must be NULL).  stats: NULL or host array[nprob].
  * Workspace: excmg_workspace_size_batched().  1 <= nprob <= 128.
  */

@@ -1485,7 +1485,46 @@ excmg_status excmg_solve_batched(int nprob, const excmg_grid* grids, const doubl
     P[i].L = prob_layout(P[i].lv, opt->precision == EXCMG_MIXED, false, mixed_min(opt));
     base += P[i].L.bytes;
   }
-  return run_excmg(P, opt, nullptr, stats, c);
+  // Problems whose finest grid has kBatchSoloNodes nodes or more run one after another,
+  // each on the whole GPU with a single solve's engines (the shared-memory CG up to 2^20
+  // nodes, every SM above); the others share the launches of one batch, where their CG
+  // runs as a team of blocks per problem.  Each problem keeps its own workspace region;
+  // the runs share the header's states in stream order.
+  std::vector<int> solo, team;
+  for (int i = 0; i < nprob; ++i) {
+    const Level& fl = P[i].lv.back();
+    const long long nodes = (long long)(fl.nx + 1) * (fl.ny + 1) * (fl.nz + 1);
+    (nodes >= kBatchSoloNodes ? solo : team).push_back(i);
+  }
+  if (solo.empty()) return run_excmg(P, opt, nullptr, stats, c);
+  excmg_status result = EXCMG_OK;
+  long long launches = 0;
+  auto run_part = [&](const std::vector<int>& idx) -> excmg_status {
+    std::vector<Prob> part;
+    for (int i : idx) part.push_back(P[i]);
+    std::vector<excmg_stats> st(idx.size());
+    const excmg_status e = run_excmg(part, opt, nullptr, stats ? st.data() : nullptr, c);
+    if (stats) {
+      launches += st[0].launches;
+      for (size_t k = 0; k < idx.size(); ++k) {
+        stats[idx[k]] = st[k];
+        stats[idx[k]].launches = 0;
+      }
+    }
+    return e;
+  };
+  for (int i : solo) {
+    const excmg_status e = run_part({i});
+    if (e != EXCMG_OK && e != EXCMG_ERR_NOT_CONVERGED) return e;
+    if (e != EXCMG_OK) result = e;
+  }
+  if (!team.empty()) {
+    const excmg_status e = run_part(team);
+    if (e != EXCMG_OK && e != EXCMG_ERR_NOT_CONVERGED) return e;
+    if (e != EXCMG_OK) result = e;
+  }
+  if (stats) stats[0].launches = launches;
+  return result;
 }
 
 excmg_status excmg_exp_finite(const excmg_grid* grid, const double* u2h, const double* u4h,

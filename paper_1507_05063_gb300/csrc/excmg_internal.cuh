@@ -250,6 +250,12 @@ bool encode_plane_map(CUtensorMap* m, float* base, const Grid3& g32);
 #define EXCMG_RESIDENT_MAX_NODES (1 << 20)
 #endif
 constexpr long long kResidentMaxNodes = EXCMG_RESIDENT_MAX_NODES;
+// excmg_solve_batched: problems with a finest grid of at least this many nodes run as
+// single solves, one after another; smaller ones share the batch's launches.
+#ifndef EXCMG_BATCH_SOLO_NODES
+#define EXCMG_BATCH_SOLO_NODES (1LL << 18)
+#endif
+constexpr long long kBatchSoloNodes = EXCMG_BATCH_SOLO_NODES;
 struct ResidentDesc {
   Grid3 g;
   Coef A;
