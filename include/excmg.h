@@ -382,8 +382,7 @@ excmg_status excmg_residual(const excmg_grid* grid, const double* f, const doubl
  *   not fit, 64 x 64 x 64 does).  A larger grid returns EXCMG_ERR_WORKSPACE before any
  *   work is enqueued.  Only EXCMG_FP64 is accepted.
  *   Set-up: the first call on each device looks up the scratch's device address (with
- *   that device current) and caches it; make that first call before any stream
- *   capture.
+ *   that device current) and caches it.
  *   Sharing: every call uses the same scratch and leaves its last contents there (the
  *   call clears what must start at zero itself).  Calls whose work overlaps on the GPU
  *   -- on different streams or from different host threads -- race on the scratch and

@@ -14,8 +14,7 @@
 //
 // In host code the array's name is only a host-side stand-in; the device address is
 // looked up with cudaGetSymbolAddress the first time the entry point runs on a device
-// (with that device current) and cached per device.  That first call on each device
-// should therefore come before any stream capture.
+// (with that device current) and cached per device.
 #include <math.h>
 #include <string.h>
 
