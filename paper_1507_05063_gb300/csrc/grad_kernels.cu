@@ -21,6 +21,7 @@ namespace excmg {
 namespace {
 
 constexpr int kTab = 64;
+constexpr int kAhead = 8;  // line steps whose loads are in flight together (strided lines)
 
 // The factors of the forward sweep written as dp_t = (u_{i+1} - u_{i-1}) A_t + B_t dp_{t-1}
 // (A_t = (1/(2h)) / m_t, B_t = -(1/6) / m_t; the first step's dp_{t-1} is D_0, the
@@ -82,38 +83,108 @@ __global__ void __launch_bounds__(kThreads)
       D1p[0] = a1;
       D1p[N * step] = n1;
     }
-    // forward sweep over unknowns t = 0..N-2 (node i = t + 1)
+    // forward sweep over unknowns t = 0..N-2 (node i = t + 1), kAhead steps at a time:
+    // the steps' loads are issued before their arithmetic, so each line has kAhead loads
+    // in flight instead of one (the recurrence only waits on the first)
     double um0 = U0[0], uc0 = U0[step], dp0 = a0;
     double um1 = U1[0], uc1 = U1[step], dp1 = a1;
-    for (int i = 1; i <= N - 1; ++i) {
-      const long long o = (long long)(i + 1) * step;
-      const double up0 = U0[o], up1 = U1[o];
+    auto fstep = [&](int i, double up0, double up1) {
       const int t = i - 1 < kTab ? i - 1 : kTab - 1;
       if (i == N - 1) {
         dp0 += n0;
         dp1 += n1;
       }
-      dp0 = fma(up0 - um0, A[t], B[t] * dp0);
-      dp1 = fma(up1 - um1, A[t], B[t] * dp1);
+      dp0 = fma(B[t], dp0, (up0 - um0) * A[t]);
+      dp1 = fma(B[t], dp1, (up1 - um1) * A[t]);
       D0p[(long long)i * step] = dp0;
       if (two) D1p[(long long)i * step] = dp1;
       um0 = uc0;
       uc0 = up0;
       um1 = uc1;
       uc1 = up1;
+    };
+    int i = 1;
+    for (; i + kAhead - 1 <= N - 1; i += kAhead) {
+      double q0[kAhead], q1[kAhead];
+#pragma unroll
+      for (int k = 0; k < kAhead; ++k) {
+        const long long o = (long long)(i + 1 + k) * step;
+        q0[k] = U0[o];
+        q1[k] = U1[o];
+      }
+#pragma unroll
+      for (int k = 0; k < kAhead; ++k) fstep(i + k, q0[k], q1[k]);
     }
-    // back substitution
+    for (; i <= N - 1; ++i) {
+      const long long o = (long long)(i + 1) * step;
+      fstep(i, U0[o], U1[o]);
+    }
+    // back substitution, likewise kAhead nodes' loads at a time
     double x0 = dp0, x1 = dp1;
-    for (int i = N - 2; i >= 1; --i) {
+    auto bstep = [&](int i, double d0, double d1) {
       const int t = i - 1 < kTab ? i - 1 : kTab - 1;
       const long long o = (long long)i * step;
-      x0 = D0p[o] - cp[t] * x0;
+      x0 = d0 - cp[t] * x0;
       D0p[o] = x0;
       if (two) {
-        x1 = D1p[o] - cp[t] * x1;
+        x1 = d1 - cp[t] * x1;
         D1p[o] = x1;
       }
+    };
+    i = N - 2;
+    for (; i - kAhead + 1 >= 1; i -= kAhead) {
+      double r0[kAhead], r1[kAhead];
+#pragma unroll
+      for (int k = 0; k < kAhead; ++k) {
+        const long long o = (long long)(i - k) * step;
+        r0[k] = D0p[o];
+        r1[k] = two ? D1p[o] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < kAhead; ++k) bstep(i - k, r0[k], r1[k]);
     }
+    for (; i >= 1; --i) {
+      const long long o = (long long)i * step;
+      bstep(i, D0p[o], two ? D1p[o] : 0.0);
+    }
+  }
+}
+
+// Copies w <= 34 consecutive nodes x0 .. x0 + w - 1 of the 32 lines L0 .. L0 + 31 (those
+// below nlines) into tile[line][0 .. w - 1], lanes along x (coalesced).  Eight lines'
+// loads are issued before their stores, so sixteen loads per lane are in flight at once
+// (a loop that stored each line before loading the next waited for every load in turn).
+// src may be written by this kernel (the forward sweep's values in `out`), so the loads
+// take the coherent path.
+__device__ __forceinline__ void stage_rows(double (*tile)[35], const double* src, long long L0,
+                                           long long nlines, long long stride, int x0, int w,
+                                           int lane) {
+  for (int l0 = 0; l0 < 32; l0 += 8) {
+    double v[8][2];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const long long Ll = L0 + l0 + k;
+      const double* row = src + (Ll < nlines ? Ll : L0) * stride + x0;
+      v[k][0] = (Ll < nlines && lane < w) ? row[lane] : 0.0;
+      v[k][1] = (Ll < nlines && lane + 32 < w) ? row[lane + 32] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      tile[l0 + k][lane] = v[k][0];
+      if (lane < 3) tile[l0 + k][32 + lane] = v[k][1];
+    }
+  }
+}
+
+// The reverse of stage_rows for w <= 32 nodes: tile[line][0 .. w - 1] to nodes
+// x0 .. x0 + w - 1 of the lines below nlines.
+__device__ __forceinline__ void unstage_rows(double (*tile)[35], double* dst, long long L0,
+                                             long long nlines, long long stride, int x0, int w,
+                                             int lane) {
+#pragma unroll 8
+  for (int l = 0; l < 32; ++l) {
+    const long long Ll = L0 + l;
+    if (Ll < nlines && lane < w) dst[Ll * stride + x0 + lane] = tile[l][lane];
   }
 }
 
@@ -145,27 +216,19 @@ __global__ void __launch_bounds__(32)
     for (int x0 = 1; x0 <= N - 1; x0 += 32) {
       const int cnt = min(32, N - x0);  // nodes x0 .. x0+cnt-1
       __syncwarp();
-      for (int l = 0; l < 32; ++l) {  // coalesced: lane = x offset
-        const long long Ll = L0 + l;
-        if (Ll >= nlines) break;
-        for (int c = lane; c < cnt + 2; c += 32) tile[l][c] = u[Ll * stride + x0 - 1 + c];
-      }
+      stage_rows(tile, u, L0, nlines, stride, x0 - 1, cnt + 2, lane);
       __syncwarp();
       if (mine) {
         for (int c = 0; c < cnt; ++c) {
           const int i = x0 + c;
           const int t = i - 1 < kTab ? i - 1 : kTab - 1;
           if (i == N - 1) dp += DN;
-          dp = fma(tile[lane][c + 2] - tile[lane][c], A[t], B[t] * dp);
+          dp = fma(B[t], dp, (tile[lane][c + 2] - tile[lane][c]) * A[t]);
           tile[lane][c] = dp;
         }
       }
       __syncwarp();
-      for (int l = 0; l < 32; ++l) {
-        const long long Ll = L0 + l;
-        if (Ll >= nlines) break;
-        for (int c = lane; c < cnt; c += 32) out[Ll * stride + x0 + c] = tile[l][c];
-      }
+      unstage_rows(tile, out, L0, nlines, stride, x0, cnt, lane);
     }
     // back substitution, chunks from the end
     double xv = 0.0;
@@ -174,11 +237,7 @@ __global__ void __launch_bounds__(32)
       const int cnt = min(32, x1);  // nodes x1-cnt+1 .. x1
       const int xs = x1 - cnt + 1;
       __syncwarp();
-      for (int l = 0; l < 32; ++l) {
-        const long long Ll = L0 + l;
-        if (Ll >= nlines) break;
-        for (int c = lane; c < cnt; c += 32) tile[l][c] = out[Ll * stride + xs + c];
-      }
+      stage_rows(tile, out, L0, nlines, stride, xs, cnt, lane);
       __syncwarp();
       if (mine) {
         for (int c = cnt - 1; c >= 0; --c) {
@@ -195,11 +254,7 @@ __global__ void __launch_bounds__(32)
       }
       last = false;
       __syncwarp();
-      for (int l = 0; l < 32; ++l) {
-        const long long Ll = L0 + l;
-        if (Ll >= nlines) break;
-        for (int c = lane; c < cnt; c += 32) out[Ll * stride + xs + c] = tile[l][c];
-      }
+      unstage_rows(tile, out, L0, nlines, stride, xs, cnt, lane);
     }
   }
 }
