@@ -855,7 +855,10 @@ def run_adjoint(X, torch, steps=3):
     out = {"workload": "adjoint source recovery on 256^3 (trig-sum target, seed 20150705), eps 1e-10",
            "steps": steps}
     for prec in ("fp64", "mixed"):
-        kw = dict(eps=1e-10, eps_coarse=1e-12, precision=prec)
+        # one workspace for every solve of the loop (the adjoint sizes its own)
+        ws = X.workspace(X.solve_workspace_bytes(L, N, N0, eps=1e-10, eps_coarse=1e-12, precision=prec),
+                         gd.device)
+        kw = dict(eps=1e-10, eps_coarse=1e-12, precision=prec, ws=ws)
         ut = X.solve(torch.from_numpy(ft).cuda(), gd, L, N0, **kw)["u"]
         # one untimed forward and backward: the allocator's first requests of this size
         fw = torch.zeros_like(ut).requires_grad_(True)
