@@ -94,6 +94,35 @@ def test_batched_matches_single_solves(X, precision):
         assert st["relres"][-1] <= eps * 1.0000001
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_solves_large_problems_alone(X, precision):
+    """excmg_solve_batched solves its problems of 2^18 nodes and more one after another as
+    single solves (a 64^3 grid: 274,625 nodes) and batches the others: the large problem's
+    result is the single solve's, bit for bit; the small ones agree with their single
+    solves far below the tolerance; every problem meets it."""
+    eps, L = 1e-10, (1.0, 1.0, 1.0)
+    specs = [((64, 64, 64), (4, 4, 4)), ((32, 16, 16), (8, 4, 4)), ((16, 32, 16), (4, 8, 4))]
+    probs = []
+    for i, (N, N0) in enumerate(specs):
+        f, g, _ = P.make_inputs(P.trig_sum(31 + i, K=8, L=L), N, L)
+        probs.append((N, N0, f, g))
+    kw = dict(eps=eps, precision=precision, autotune=-1)
+    if precision == "mixed":
+        kw["mixed_min_nodes"] = 1 << 12
+    batch = [X.BatchedProblem(L, N, N0, dev(f), dev(g)) for N, N0, f, g in probs]
+    res = X.solve_batched(batch, **kw)
+    assert res["status"] == "EXCMG_OK"
+    for k, ((N, N0, f, g), ub, st) in enumerate(zip(probs, res["u"], res["stats"])):
+        single = X.solve(dev(f), dev(g), L, N0, **kw)
+        a, b = host(ub), host(single["u"])
+        if k == 0:
+            assert np.array_equal(a, b)
+            assert st["iters"] == single["stats"]["iters"]
+        else:
+            assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b)) + 1e-12
+        assert st["relres"][-1] <= eps * 1.0000001
+
+
 def test_batched_replays_oracle(X):
     """Each batched problem against the oracle run with the batch's iteration counts."""
     probs = _batch(7, 3, (16, 32))
