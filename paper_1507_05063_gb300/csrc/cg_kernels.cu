@@ -451,25 +451,27 @@ __device__ __forceinline__ double update_flat(const CGDesc<T>& d, int bl, int G,
 
 // ---------------------------------------------------------------------------------
 // Tensor-copy staging of the float32 stencil (the MIXED inner solves).  A block's
-// stencil planes -- r and p_old of (kTX + 8) x (kTY + 2) nodes, the tile's columns with
+// stencil planes -- r and p_old of (kTX + 8) x (kTileY + 2) nodes, the tile's columns with
 // a one-node halo in y and a 16-byte aligned halo of four in x -- stream through a ring
 // of kStages shared-memory stages: thread 0 issues the two cp.async.bulk.tensor copies
 // of a plane kStages planes ahead, and a "full" mbarrier per stage counts their bytes.
 // No register holds a load and no block barrier separates the planes: every thread forms
-// the nine p_new = sigma r + beta p_old values of its 3x3 neighbourhood straight from the
-// stage, each warp releases the stage through an "empty" mbarrier when it is done with
+// the p_new = sigma r + beta p_old values of its (rows + 2) x 3 neighbourhood straight
+// from the stage, each warp releases the stage through an "empty" mbarrier when it is done with
 // it, and thread 0 refills a stage once all warps have released it -- so warps drift
 // apart by up to kStages planes and hide each other's latencies.  Out-of-range boxes
 // (x < 0, y < 0, planes -1 and nz + 1, the padding columns) read as zeros.
 // ---------------------------------------------------------------------------------
+// Two rows per thread (tiles of 32 x 16 columns) in boxes of four planes: 9% faster per
+// step than one row in boxes of six on 512x256x128, the same on 1024x512x512.
 #ifndef EXCMG_TMA_ROWS
-#define EXCMG_TMA_ROWS 1
+#define EXCMG_TMA_ROWS 2
 #endif
 #ifndef EXCMG_TMA_STAGES
 #define EXCMG_TMA_STAGES 3
 #endif
 #ifndef EXCMG_TMA_PLANES
-#define EXCMG_TMA_PLANES 6
+#define EXCMG_TMA_PLANES 4
 #endif
 constexpr int kRT = EXCMG_TMA_ROWS;        // y-rows per thread (consecutive)
 constexpr int kTileY = kTY * kRT;          // y-rows of a tile of this engine

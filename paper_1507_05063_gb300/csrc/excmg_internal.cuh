@@ -110,7 +110,8 @@ int choose_tz(const Grid3& g, int grid_blocks, int requested);
 
 // Tensor maps of one float32 CG problem (cp.async.bulk.tensor): r and the two p buffers,
 // each a 3D map of the padded array (x extent nx + 1, so the padding reads as zero) with
-// a box of one stencil plane (kTX + 8) x (kTY + 2) x 1.
+// a box of a tile's columns and their halo over several planes ((kTX + 8) x (rows of a
+// tile + 2) x planes per copy: cg_kernels.cu).
 struct alignas(64) TmapSet {
   CUtensorMap r, pa, pb;
 };
